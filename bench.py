@@ -1,0 +1,479 @@
+"""Benchmark: Bellman action evaluations per second of the storage DP.
+
+One step = one pass of the whole hot path over the 5-minute real-time
+workload (T=288, N=1001, K=20, A=201, two modes): the persistent
+backward-induction sweep (EV contraction + banded max-plus + argmax policy,
+all stages in one launch) followed by the convexified bid curves of every
+(t, mode, k).  Inputs are synthetic (seeded generators).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Bellman evals/s (T*N*K*A / sweep s)"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["esdp", "reference"], default="esdp")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the large-asset, portfolio and adjoint sub-benchmarks")
+    ap.add_argument("--only", default="", help="run one sub-benchmark: config3|config4|config5")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def alu_peak_evals(n_sm: int, mhz: float) -> float:
+    """FP32-pipe ceiling: 128 lanes per SM, one add and one max per
+    evaluation, so n_sm * 128 * f / 2 evaluations per second."""
+    return n_sm * 128 * mhz * 1e6 / 2.0
+
+
+class L2Flush:
+    def __init__(self, torch, mb=512):
+        self.buf = torch.empty(mb * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.buf.zero_()
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args, rank):
+    """FP64 CPU oracle on the same step: full solve (policy kept) + the
+    envelope of every (t, m, k)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2511_15629_b300 import instances as I
+    inst = I.config2()
+    cores = host_cores()
+
+    def step():
+        r = O.solve(inst, keep_EV=True, nthreads=cores)
+        O.bid_curves(inst, r["EV"])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = inst.evals * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "config2: T=288 N=1001 K=20 A=201 modes=2 + bid curves",
+                   "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full steps (solve + envelopes)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm
+
+def cpu_baseline_c2():
+    """The oracle as it stands, one full config2 step on all host cores."""
+    from oracle import oracle as O
+    from paper_2511_15629_b300 import instances as I
+    inst = I.config2()
+    cores = host_cores()
+    t0 = time.perf_counter()
+    r = O.solve(inst, keep_EV=True, nthreads=cores)
+    O.bid_curves(inst, r["EV"])
+    dt = time.perf_counter() - t0
+    return {"value": inst.evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one full config2 step (FP64 solve with policy + 11520 envelopes), "
+                      f"{dt:.1f} s"}
+
+
+def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
+    """Per-step CUDA-event timing on `stream`, L2 flushed (untimed) between
+    steps.  Returns (total step seconds, per-mark seconds list)."""
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(marks + 1)] for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush()
+            step(ev[i])
+    torch.cuda.synchronize()
+    per_mark = [0.0] * marks
+    for i in range(steps):
+        for j in range(marks):
+            per_mark[j] += ev[i][j].elapsed_time(ev[i][j + 1]) / 1e3
+    return sum(per_mark), per_mark
+
+
+def run_esdp(args, rank, world):
+    import torch
+    from paper_2511_15629_b300 import esdp as E
+    from paper_2511_15629_b300 import instances as I
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    stream = torch.cuda.Stream()
+    flush = L2Flush(torch)
+    out = {}
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2032.0))
+
+    if args.only:
+        extras = {args.only: EXTRAS[args.only](torch, E, I, stream, flush, args, n_sm, f_max)}
+        if rank == 0:
+            print(json.dumps({"extra": extras}), flush=True)
+        return
+
+    # ---- the main workload (config2 step: sweep + bid curves)
+    inst = I.config2()
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    MNK = inst.n_modes * inst.N * inst.K
+    V1 = torch.empty(MNK, device="cuda")
+    nh = inst.T * inst.n_modes * inst.K
+    n_bp = torch.empty(nh, dtype=torch.int32, device="cuda")
+    idx = torch.empty(nh * inst.N, dtype=torch.int32, device="cuda")
+    slope = torch.empty(nh * inst.N, dtype=torch.float32, device="cuda")
+    s = E.Solver([inst], device_ptrs=True, keep_ev=True)
+    s.autotune(stream=stream)
+    torch.cuda.synchronize()
+
+    def step(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+        if evs:
+            evs[1].record(st)
+        s.bid_curves(0, 1, inst.T + 1, n_bp, idx, slope, stream=st)
+        if evs:
+            evs[2].record(st)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        total, (t_sweep, t_hull) = time_steps(torch, step, args.steps, args.warmup, stream,
+                                              flush, marks=2)
+    torch.cuda.synchronize()
+    assert s.status(stream=stream) == 0, "device status after the timed steps"
+    t_local = torch.tensor([total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    total = float(t_local.item())
+    value = inst.evals * args.steps * world / total
+    sweep_evals_s = inst.evals * args.steps / t_sweep
+    peak = alu_peak_evals(n_sm, f_max)
+    clocks = clk.summary()
+    roof = {"bound": "alu", "achieved": sweep_evals_s / 1e9, "peak": peak / 1e9,
+            "unit": "Gevals/s", "frac": sweep_evals_s / peak, "traffic": None,
+            "kernel": "sweep_kernel", "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x "
+            f"{f_max:.0f} MHz / 2 ops per evaluation (max clock)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = sweep_evals_s / alu_peak_evals(n_sm, clocks["sm_mhz"])
+    info = s.launch_info()
+
+    # ---- end to end through the host-pointer API (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in cat.items()}
+        hp = {k: v.numpy() for k, v in pin.items()}
+        hV1 = torch.empty(MNK, dtype=torch.float32).pin_memory().numpy()
+        hn = torch.empty((inst.T, inst.n_modes, inst.K), dtype=torch.int32).pin_memory().numpy()
+        hidx = torch.empty((inst.T, inst.n_modes, inst.K, inst.N),
+                           dtype=torch.int32).pin_memory().numpy()
+        hsl = torch.empty((inst.T, inst.n_modes, inst.K, inst.N),
+                          dtype=torch.float32).pin_memory().numpy()
+        hs = E.Solver([inst], keep_ev=True, no_validate=True)
+        hs.autotune()
+
+        def host_step():
+            hs.solve(hp["price"], hp["trans"], hp["cost"], hp["terminal"], hV1)
+            hs.bid_curves(0, 1, inst.T + 1, hn, hidx, hsl)
+        for _ in range(args.warmup):
+            host_step()
+        times = []
+        for _ in range(args.steps):
+            flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            host_step()
+            times.append(time.perf_counter() - t0)
+        h2d = sum(v.nbytes for v in hp.values())
+        d2h = hV1.nbytes + hn.nbytes + hidx.nbytes + hsl.nbytes
+        e2e = {"value": inst.evals / (sum(times) / len(times)), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": sum(times) / len(times) * 1e3}
+        hs.close()
+
+    extras = {}
+    if not args.no_extras:
+        for name, fn in EXTRAS.items():
+            try:
+                extras[name] = fn(torch, E, I, stream, flush, args, n_sm, f_max)
+            except Exception as ex:  # keep the main line even if a sub-benchmark fails
+                extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
+
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline_c2()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "config2: T=288 N=1001 K=20 A=201 modes=2, sweep + bid "
+                                   "curves of every (t,m,k)",
+                       "evals_per_step": inst.evals, "l2": "flushed between steps (512 MB)",
+                       "parallelism": f"replicas x{world}", "launch": info},
+            "sweep_ms": t_sweep / args.steps * 1e3, "bid_curves_ms": t_hull / args.steps * 1e3,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 2 * args.steps, "extra": extras,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------- sub-benchmarks
+
+def bench_config3(torch, E, I, stream, flush, args, n_sm, f_max):
+    """Large single asset: the persistent sweep alone (policy kept)."""
+    inst = I.config3()
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    V1 = torch.empty(inst.N * inst.K, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    s.autotune(stream=stream)
+
+    def step(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+        if evs:
+            evs[1].record(st)
+    n = max(3, min(args.steps, 5))
+    total, _ = time_steps(torch, step, n, 2, stream, flush)
+    ev_s = inst.evals * n / total
+    peak = alu_peak_evals(n_sm, f_max)
+    info = s.launch_info()
+    s.close()
+    return {"evals_per_s": ev_s, "ms": total / n * 1e3, "frac_alu": ev_s / peak,
+            "launch": info, "steps": n}
+
+
+def bench_config4(torch, E, I, stream, flush, args, n_sm, f_max):
+    """256 heterogeneous assets in one graph-captured persistent launch,
+    against 256 sequential single-asset solves."""
+    assets = I.config4(256)
+    evals = sum(a.evals for a in assets)
+    cat = E.concat_inputs(assets)
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    V1 = torch.empty(sum(a.n_modes * a.N * a.K for a in assets), device="cuda")
+    s = E.Solver(assets, device_ptrs=True)
+    s.autotune(stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=stream)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1,
+                stream=torch.cuda.current_stream())
+
+    def step(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        g.replay()
+        if evs:
+            evs[1].record(st)
+    n = max(3, min(args.steps, 5))
+    total, _ = time_steps(torch, step, n, 2, stream, flush)
+    batched = evals * n / total
+    assert s.status(stream=stream) == 0
+    # sequential plain solves, one context per asset
+    solos = []
+    for a in assets:
+        c1 = E.concat_inputs([a])
+        solos.append((E.Solver([a], device_ptrs=True),
+                      {k: torch.from_numpy(v).to("cuda") for k, v in c1.items()},
+                      torch.empty(a.n_modes * a.N * a.K, device="cuda")))
+    torch.cuda.synchronize()
+
+    def seq(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        for so, dd, vv in solos:
+            so.solve(dd["price"], dd["trans"], dd["cost"], dd["terminal"], vv, stream=st)
+        if evs:
+            evs[1].record(st)
+    total_seq, _ = time_steps(torch, seq, 2, 1, stream, flush)
+    sequential = evals * 2 / total_seq
+    info = s.launch_info()
+    for so, _, _ in solos:
+        so.close()
+    s.close()
+    return {"evals_per_s": batched, "ms": total / n * 1e3, "frac_alu":
+            batched / alu_peak_evals(n_sm, f_max), "sequential_evals_per_s": sequential,
+            "sequential_ms": total_seq / 2 * 1e3, "speedup_vs_sequential": batched / sequential,
+            "evals_per_step": evals, "launch": info}
+
+
+def bench_config5(torch, E, I, stream, flush, args, n_sm, f_max):
+    """Adjoint: forward solve (int16 policy, checkpoints every 32) + gradient
+    against the plain solve of the same asset."""
+    inst = I.config5()
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    V1 = torch.empty(inst.N * inst.K, device="cuda")
+    mu0 = torch.from_numpy(inst.mu0).to("cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    dp = torch.empty(inst.T * inst.K, device="cuda")
+    dt = torch.empty(inst.T * inst.K * inst.K, device="cuda")
+    de = torch.empty(2, dtype=torch.float64, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    s.autotune(stream=stream)
+
+    def plain(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+        if evs:
+            evs[1].record(st)
+
+    def adjoint(evs):
+        st = torch.cuda.current_stream()
+        if evs:
+            evs[0].record(st)
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+        s.grad(0, mu0, J, dp, dt, de, stream=st)
+        if evs:
+            evs[1].record(st)
+    n = max(3, min(args.steps, 5))
+    t_plain, _ = time_steps(torch, plain, n, 2, stream, flush)
+    t_adj, _ = time_steps(torch, adjoint, n, 2, stream, flush)
+    s.close()
+    return {"plain_ms": t_plain / n * 1e3, "forward_plus_adjoint_ms": t_adj / n * 1e3,
+            "adjoint_over_plain": t_adj / t_plain,
+            "plain_evals_per_s": inst.evals * n / t_plain}
+
+
+EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    run_esdp(args, rank, world)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * esdp.h -- C ABI of the B300 (sm_103a) stochastic-DP library for energy
+ * storage arbitrage.
+ *
+ * The library solves the discretized multistage stochastic storage problem
+ * by backward induction (Sec. III-B, Algorithm 1), generalised from
+ * stagewise-independent price samples (eq. 14) to a Markov chain of price
+ * states with per-stage transition matrices:
+ *
+ *   stages t = 1..T; SoC grid s = 0..N-1 with step delta = s_max/(N-1)
+ *   (eq. 12); price state k = 0..K-1 with price price[t][k]; optional mode
+ *   m in {0,1} (1 iff the most recent non-idle action was a charge).
+ *   Action a = 0..A-1 shifts the SoC by d = a - D_dis grid steps (the integer
+ *   "recombining" interior of the action grid of eq. 13), A = D_dis+D_chg+1.
+ *   Grid energy (eq. 2 with separate efficiencies):
+ *       e_a = -d*delta*eta_d (d < 0, discharge)   e_a = -d*delta/eta_c (d > 0)
+ *   Expectation (eq. 6):  EV_t[m][s][k] = sum_k2 trans[t][k][k2] V_{t+1}[m][s][k2]
+ *   Bellman step (eq. 5 over the feasible set of eq. 4, 0 <= s+d <= N-1):
+ *       V_t[m][s][k] = max_a  price[t][k]*e_a - cost[a]
+ *                             - switch_cost*[m==1 && d<0] + EV_t[m'][s+d][k]
+ *   with m' = 0 after a discharge, 1 after a charge, m when idle; the policy
+ *   is the smallest maximising a.  V_{T+1} = terminal (zero in eq. 6).
+ *   Bid curves (eq. 10-11): the upper concave envelope of EV_t[m][.][k]
+ *   over the SoC grid; its slopes are the monotone marginal values.
+ *
+ * Array layouts (row-major, float32 unless stated, per asset, assets
+ * concatenated in the order given to esdp_create):
+ *   price    [T][K]            trans [T][K][K]   (trans[t] maps stage t -> t+1)
+ *   cost     [A]               terminal [n_modes][N][K]
+ *   V1       [n_modes][N][K]   policy [n_modes][N][K] per stage (int32/int16)
+ *
+ * Ownership and errors: the caller owns every buffer it passes; the context
+ * owns its device workspace.  Without ESDP_DEVICE_PTRS all pointers are host
+ * pointers and every call blocks until its result is in host memory; with
+ * it, the array arguments of esdp_solve / esdp_grad are device pointers, the
+ * work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and the caller must keep the input buffers alive and unchanged until the
+ * last call that uses them (esdp_grad and esdp_bid_curves read them again).
+ * Every function returns ESDP_OK (0) or a negative ESDP_E* code and leaves a
+ * message for esdp_last_error.  A call that fails leaves the context usable
+ * unless the code is ESDP_ECUDA.
+ */
+#ifndef ESDP_H_
+#define ESDP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESDP_OK 0
+#define ESDP_EINVAL (-1)   /* bad shape, efficiency outside (0,1], negative
+                              transition entry, NaN/Inf input, bad index */
+#define ESDP_ENOMEM (-2)   /* device or host allocation failed */
+#define ESDP_ECUDA (-3)    /* a CUDA call failed (message has the reason) */
+#define ESDP_ETIMEOUT (-4) /* a device-side wait gave up (bounded spin) */
+#define ESDP_ESTATE (-5)   /* result requested before the solve that makes it,
+                              or not kept by the context's flags */
+#define ESDP_ENUMERIC (-6) /* the solve produced a NaN */
+
+/* esdp_create flags */
+#define ESDP_DEVICE_PTRS 1u /* array arguments are device pointers, stream-ordered */
+#define ESDP_KEEP_EV 2u     /* keep EV_t of every stage (esdp_bid_curves,
+                               esdp_expected_value) */
+#define ESDP_CHECK_ROWS 4u  /* reject transition rows whose sum is not 1 +- 1e-5 */
+#define ESDP_NO_VALIDATE 8u /* skip the host-side NaN / sign scan of inputs
+                               (only meaningful with host pointers) */
+
+typedef struct esdp_ctx esdp_ctx;
+
+typedef struct {
+  int32_t T, N, K, A;     /* stages, SoC points, price states, actions */
+  int32_t D_dis, D_chg;   /* action band: shifts -D_dis..+D_chg, A = D_dis+D_chg+1 */
+  int32_t n_modes;        /* 1, or 2 = charge->discharge switch-cost flag */
+  int32_t policy_bytes;   /* 4 (int32), 2 (int16) or 0 (policy not kept) */
+  int32_t ckpt_every;     /* 0: keep the whole policy; C > 0: keep V every C
+                             stages, esdp_grad recomputes policies per segment */
+  int32_t s0;             /* initial SoC index of the objective J (esdp_grad) */
+  double s_max;           /* MWh; delta = s_max/(N-1) */
+  double tau;             /* stage length in hours (bid quantities in MW) */
+  double eta_c, eta_d;    /* charge / discharge efficiency, in (0,1] */
+  double switch_cost;     /* $ per charge->discharge switch (n_modes == 2) */
+} esdp_asset;
+
+/* Create a context for `n_assets` assets solved together (one persistent,
+ * batched launch).  Validates the shapes, allocates the device workspace on
+ * the current CUDA device and picks tile shapes (see esdp_autotune). */
+int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp_ctx** out);
+
+/* Backward induction over all assets (Algorithm 1, eq. 5-6).
+ * price [sum T*K], trans [sum T*K*K], cost [sum A], terminal [sum M*N*K]
+ * in; V1 [sum M*N*K] out (may be NULL).  Policies (and EV_t with
+ * ESDP_KEEP_EV) stay in the context.  ESDP_ETIMEOUT if a device wait gave up,
+ * ESDP_ENUMERIC if V_1 holds a NaN (host-pointer mode only). */
+int esdp_solve(esdp_ctx* ctx, const float* price, const float* trans, const float* cost,
+               const float* terminal, float* V1, void* stream);
+
+/* Policy of stage t (1..T) of `asset`: [n_modes][N][K] action indices as
+ * int32 or int16 (policy_bytes).  ESDP_ESTATE when the context keeps no full
+ * policy (policy_bytes == 0 or ckpt_every > 0) or before esdp_solve. */
+int esdp_policy(esdp_ctx* ctx, int32_t asset, int32_t t, void* out, void* stream);
+
+/* EV_t (1..T) of `asset`: [n_modes][N][K] float (needs ESDP_KEEP_EV). */
+int esdp_expected_value(esdp_ctx* ctx, int32_t asset, int32_t t, float* out, void* stream);
+
+/* Convexified bid curves (eq. 10-11) of stages t0 <= t < t1 (1-based): for
+ * every (t, m, k) the vertices of the upper concave envelope of
+ * EV_t[m][.][k] over the SoC grid, strictly-above-chord vertices only, both
+ * ends always included.  Outputs, with n = t1 - t0:
+ *   n_bp   [n][n_modes][K]      vertex count
+ *   bp_idx [n][n_modes][K][N]   vertex SoC indices (first n_bp valid)
+ *   slope  [n][n_modes][K][N]   envelope slope between vertices q and q+1 in
+ *                               $ per MWh of stored energy (first n_bp-1 valid);
+ *                               strictly decreasing (monotone bids).
+ * Needs ESDP_KEEP_EV.  Device or host pointers as the context's flags say. */
+int esdp_bid_curves(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
+                    int32_t* bp_idx, float* slope, void* stream);
+
+/* Objective J = sum_k mu0[k] V_1[0][s0][k] and its sensitivities by a
+ * forward pass of the state-occupancy distribution under the stored argmax
+ * policy (envelope theorem on eq. 5-6; exact away from ties).  With
+ * ckpt_every = C > 0 the policies are recomputed segment by segment from the
+ * V checkpoints; otherwise the whole horizon is recomputed once.  Uses the
+ * inputs of the last esdp_solve.  mu0 [K] in; J [1] (double), d_price [T*K],
+ * d_trans [T*K*K] (float), d_eta [2] (double: dJ/deta_c, dJ/deta_d) out;
+ * any output may be NULL. */
+int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* d_price,
+              float* d_trans, double* d_eta, void* stream);
+
+/* Re-time the candidate tile shapes / actions-per-warp on the device and
+ * keep the fastest (results are cached per shape class for the process). */
+int esdp_autotune(esdp_ctx* ctx, void* stream);
+
+/* Device status word of the last launch: 0, or the ESDP_E* code a kernel
+ * reported.  Synchronises `stream`. */
+int esdp_status(esdp_ctx* ctx, void* stream);
+
+/* Counters of the chosen launch shape: grid, block, work items, rows per
+ * tile of asset 0, actions split (parts), R (rows per thread).  Any may be NULL. */
+int esdp_launch_info(const esdp_ctx* ctx, int32_t* grid, int32_t* block, int32_t* items,
+                     int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread);
+
+void esdp_destroy(esdp_ctx* ctx);
+const char* esdp_last_error(const esdp_ctx* ctx);
+int esdp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESDP_H_ */

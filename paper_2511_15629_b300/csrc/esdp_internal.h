@@ -1,0 +1,135 @@
+// Internal structures shared by the host library and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace esdp {
+
+// Rows of the SoC grid a thread owns in the banded max-plus (its register
+// window), one launch uses one value.
+constexpr int kRowsPerThreadChoices[] = {4, 8, 12, 16};
+constexpr int kMaxBlock = 512;
+constexpr int kMaxWaits = 64;     // neighbour tiles a work item may wait on
+
+// Per-asset parameters of one sweep launch (device-resident array).
+struct AssetDev {
+  int T, N, K, A, D_dis, D_chg, M;
+  int policy_bytes;     // 0, 2, 4
+  int nb;               // row blocks (of R rows) per tile
+  int parts;            // the action chunks are split over this many thread groups
+  int W;                // rows per tile = nb * R
+  int n_tiles;
+  int flag_base;        // first flag of this asset
+  int wait_lo, wait_hi; // neighbour tiles [tile+wait_lo, tile+wait_hi] read our rows / we read theirs
+  int t_hi, t_lo;       // stages swept: t_hi down to t_lo
+  int ev_keep;          // 1: EV_t at ev + (t-1)*MNK; 0: double buffer ev + (t&1)*MNK
+  int policy_t_base;    // policy of stage t at policy + (t - policy_t_base)*MNK
+  int ckpt_every;       // > 0: V_t with (t-1) % C == 0, t > 1 -> ckpt[(t-1)/C - 1]
+  int rows;             // EV tile rows in shared memory: W + A + R
+  int rs;               // row stride of the payoff table (odd)
+  float sw;             // switch cost
+  // offsets into the launch's concatenated inputs (elements)
+  long long off_price, off_trans, off_cost, off_terminal, off_v1;
+  const float* e;       // [A] grid energy of each action (device)
+  const float* v_start; // V_{t_hi+1} [M][N][K]; nullptr -> terminal input
+  float* ev;            // EV buffers [*][M][N][K]
+  void* policy;         // policy buffers or nullptr
+  float* v_keep;        // V_t, t in [t_lo, t_hi], at (t - t_lo); or nullptr
+  float* ckpt;          // checkpoints or nullptr
+  // Level offsets.  The float32 working values are V'_t = V_t - c_t with a
+  // scalar c_t per stage carried in double: c_t = c_{t+1} + EV'_t[ref].
+  // EV_t = EV'_t + c_{t+1} rho_t[k] with rho_t[k] the row sums of P_t.
+  int ref_tile;         // tile holding the reference row
+  int ref_row;          // reference SoC row (mode 0, price state 0)
+  float* ref_hist;      // [T+2]: EV'_t[0][ref_row][0] of every stage (one slot per stage)
+  double* rho;          // [T][K] row sums of trans (double)
+  double* off;          // [T+2]: off[t] = c_t (written by tile 0)
+  double* evoff;        // [T][K]: EV_t - EV'_t = c_{t+1} rho_t[k] (written by tile 0)
+  const double* c_start;  // c_{t_hi+1}, or nullptr for 0
+};
+
+struct WorkItem {
+  int asset, tile, s0, s1;  // rows [s0, s1) of the asset's SoC grid
+};
+
+struct SweepParams {
+  const AssetDev* assets;
+  const WorkItem* items;
+  const int* cta_items;      // [grid + 1] prefix offsets into items
+  const float* price;        // concatenated inputs
+  const float* trans;
+  const float* cost;
+  const float* terminal;
+  float* v1;                 // concatenated V_1 output or nullptr
+  int n_steps;               // max over assets of t_hi - t_lo + 1
+  int* flags;                // one per (asset, tile), zero at launch
+  int* status;               // 0 or an ESDP_E* code
+  unsigned long long timeout_ns;
+  int wait_extra;            // 0; > 0 only in the stall test: waits for a value nobody publishes
+  double* item_c;            // [items] running level c of each work item
+  // shared-memory carve-up (floats)
+  int sm_E, sm_R, sm_V, sm_P, sm_X;
+};
+
+// Launch shape of one sweep.
+struct SweepShape {
+  int R = 8;
+  int block = 256;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+cudaError_t launch_sweep(const SweepShape& shape, const SweepParams& p, cudaStream_t stream);
+int sweep_max_blocks_per_sm(int R, int block, size_t smem);
+// Row sums (double) of every transition matrix of the launch's assets.
+cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows, const float* trans,
+                           cudaStream_t stream);
+// out[m][s][k] = EV'_t + evoff_t[k] rounded to float (the reported EV_t).
+cudaError_t launch_ev_readout(const float* evp, const double* evoff, int M, int N, int K, float* out,
+                              cudaStream_t stream);
+
+// Bid-curve envelope kernel.
+struct HullParams {
+  const float* ev;   // EV'_t of stage t0 at ev, stage stride MNK, layout [M][N][K]
+  const double* evoff;  // [n_t][K]: EV_t = float(EV'_t + evoff)
+  int n_t, M, N, K;
+  double delta;      // SoC step (MWh): slopes in $ per MWh
+  int* n_bp;         // [n_t][M][K]
+  int* idx;          // [n_t][M][K][N]
+  float* slope;      // [n_t][M][K][N]
+};
+cudaError_t launch_hull(const HullParams& p, cudaStream_t stream);
+
+// Occupancy adjoint kernels.
+struct OccParams {
+  int N, K, M, A, D_dis, t_lo, t_hi;
+  int grid_rows;          // rows (m*N + s) per CTA
+  double delta, eta_c, eta_d;
+  float sw;
+  const float* price;     // [T][K] of this asset
+  const float* trans;     // [T][K][K]
+  const float* cost;      // [A]
+  const float* e;         // [A]
+  const void* policy;     // stages t_lo..t_hi, [C][M][N][K]
+  int policy_bytes;
+  float* rho;             // [M][N][K], holds rho_{t_lo} on entry, rho_{t_hi+1} on exit
+  float* post;            // [C][M][N][K], zero on entry
+  double* d_price;        // [T][K] (accumulated)
+  double* acc;            // [4]: d_eta_c, d_eta_d, J_occ (expected reward), mass
+  int* bar;               // grid barrier counter (zero on entry)
+  int* status;
+  unsigned long long timeout_ns;
+};
+cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream);
+
+struct DTransParams {
+  int n_t, MN, K;
+  const float* post;    // [n_t][MN][K]
+  const float* vnext;   // V'_{t+1} for the n_t stages: [n_t][MN][K]
+  const double* cnext;  // [n_t]: c_{t+1}, V_{t+1} = V'_{t+1} + c_{t+1}
+  float* d_trans;       // [n_t][K][K]
+};
+cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream);
+
+}  // namespace esdp

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in include/esdp.h (libesdp.so).
+
+Argument marshalling only: every step of the solve, the bid curves and the
+adjoint runs in the CUDA library.  There is no fallback: if the library is
+missing or the device is absent the calls raise.
+
+Two calling conventions, chosen per context:
+  * host mode (default): numpy float32 arrays in and out, calls block;
+  * device mode (``device_ptrs=True``): torch CUDA tensors (or raw device
+    addresses), work queued on the given stream (default: torch's current
+    stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libesdp.so")
+
+ESDP_OK = 0
+ESDP_EINVAL = -1
+ESDP_ENOMEM = -2
+ESDP_ECUDA = -3
+ESDP_ETIMEOUT = -4
+ESDP_ESTATE = -5
+ESDP_ENUMERIC = -6
+
+ESDP_DEVICE_PTRS = 1
+ESDP_KEEP_EV = 2
+ESDP_CHECK_ROWS = 4
+ESDP_NO_VALIDATE = 8
+
+EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
+           "esdp_grad", "esdp_autotune", "esdp_status", "esdp_launch_info", "esdp_destroy",
+           "esdp_last_error", "esdp_version"]
+
+
+class EsdpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"esdp error {code}: {msg}")
+        self.code = code
+
+
+class Asset(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("N", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("A", ctypes.c_int32), ("D_dis", ctypes.c_int32), ("D_chg", ctypes.c_int32),
+                ("n_modes", ctypes.c_int32), ("policy_bytes", ctypes.c_int32),
+                ("ckpt_every", ctypes.c_int32), ("s0", ctypes.c_int32),
+                ("s_max", ctypes.c_double), ("tau", ctypes.c_double), ("eta_c", ctypes.c_double),
+                ("eta_d", ctypes.c_double), ("switch_cost", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libesdp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2511_15629_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    i32 = ctypes.c_int32
+    lib.esdp_create.argtypes = [ctypes.POINTER(Asset), i32, ctypes.c_uint32, ctypes.POINTER(vp)]
+    lib.esdp_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.esdp_policy.argtypes = [vp, i32, i32, vp, vp]
+    lib.esdp_expected_value.argtypes = [vp, i32, i32, vp, vp]
+    lib.esdp_bid_curves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.esdp_autotune.argtypes = [vp, vp]
+    lib.esdp_status.argtypes = [vp, vp]
+    lib.esdp_launch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 6
+    lib.esdp_destroy.argtypes = [vp]
+    lib.esdp_destroy.restype = None
+    lib.esdp_last_error.argtypes = [vp]
+    lib.esdp_last_error.restype = ctypes.c_char_p
+    lib.esdp_version.argtypes = []
+    for name in EXPORTS:
+        if name not in ("esdp_destroy", "esdp_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def asset_from_instance(inst) -> Asset:
+    return Asset(T=inst.T, N=inst.N, K=inst.K, A=inst.A, D_dis=inst.D_dis, D_chg=inst.D_chg,
+                 n_modes=inst.n_modes, policy_bytes=inst.policy_bytes,
+                 ckpt_every=inst.ckpt_every, s0=inst.s0, s_max=inst.s_max, tau=inst.tau,
+                 eta_c=inst.eta_c, eta_d=inst.eta_d, switch_cost=inst.switch_cost)
+
+
+def concat_inputs(instances: Sequence) -> dict:
+    """Concatenate the per-asset float32 inputs in asset order."""
+    cat = lambda name: np.ascontiguousarray(
+        np.concatenate([getattr(i, name).ravel() for i in instances]).astype(np.float32))
+    return {"price": cat("price"), "trans": cat("trans"), "cost": cat("cost"),
+            "terminal": cat("terminal")}
+
+
+def _host_ptr(a: Optional[np.ndarray], dtype) -> Optional[int]:
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous, \
+        "expected a C-contiguous numpy array of " + str(dtype)
+    return a.ctypes.data
+
+
+def _dev_ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    assert a.is_cuda and a.is_contiguous(), "expected a contiguous CUDA tensor"
+    return a.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Solver:
+    """One esdp context over a list of assets (instances)."""
+
+    def __init__(self, instances: Sequence, *, device_ptrs: bool = False, keep_ev: bool = False,
+                 check_rows: bool = False, no_validate: bool = False):
+        self._lib = load_library()
+        self.instances = list(instances)
+        self.device = device_ptrs
+        flags = ((ESDP_DEVICE_PTRS if device_ptrs else 0) | (ESDP_KEEP_EV if keep_ev else 0)
+                 | (ESDP_CHECK_ROWS if check_rows else 0) | (ESDP_NO_VALIDATE if no_validate else 0))
+        arr = (Asset * len(self.instances))(*[asset_from_instance(i) for i in self.instances])
+        self._ctx = ctypes.c_void_p()
+        rc = self._lib.esdp_create(arr, len(self.instances), flags, ctypes.byref(self._ctx))
+        if rc != ESDP_OK:
+            msg = self.last_error()
+            self.close()
+            raise EsdpError(rc, msg)
+
+    # -- helpers ---------------------------------------------------------
+    def last_error(self) -> str:
+        if not self._ctx:
+            return "no context"
+        return self._lib.esdp_last_error(self._ctx).decode()
+
+    def _check(self, rc: int):
+        if rc != ESDP_OK:
+            raise EsdpError(rc, self.last_error())
+
+    def _ptr(self, a, dtype=np.float32):
+        return _dev_ptr(a) if self.device else _host_ptr(a, dtype)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.esdp_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API -------------------------------------------------------------
+    def solve(self, price, trans, cost, terminal, V1=None, stream=None):
+        self._check(self._lib.esdp_solve(self._ctx, self._ptr(price), self._ptr(trans),
+                                         self._ptr(cost), self._ptr(terminal), self._ptr(V1),
+                                         _stream(stream)))
+        return V1
+
+    def solve_instances(self, V1: Optional[np.ndarray] = None) -> np.ndarray:
+        """Host mode: solve the context's own instances, return V1 per asset."""
+        assert not self.device
+        cat = concat_inputs(self.instances)
+        n = sum(i.n_modes * i.N * i.K for i in self.instances)
+        V1 = np.empty(n, np.float32) if V1 is None else V1
+        self.solve(cat["price"], cat["trans"], cat["cost"], cat["terminal"], V1)
+        out, o = [], 0
+        for i in self.instances:
+            L = i.n_modes * i.N * i.K
+            out.append(V1[o:o + L].reshape(i.n_modes, i.N, i.K))
+            o += L
+        return out
+
+    def policy(self, asset: int, t: int, out=None, stream=None):
+        inst = self.instances[asset]
+        if out is None:
+            assert not self.device
+            dt = np.int16 if inst.policy_bytes == 2 else np.int32
+            out = np.empty((inst.n_modes, inst.N, inst.K), dt)
+        dtype = out.dtype if isinstance(out, np.ndarray) else None
+        p = _dev_ptr(out) if self.device else _host_ptr(out, dtype)
+        self._check(self._lib.esdp_policy(self._ctx, asset, t, p, _stream(stream)))
+        return out
+
+    def expected_value(self, asset: int, t: int, out=None, stream=None):
+        inst = self.instances[asset]
+        if out is None:
+            assert not self.device
+            out = np.empty((inst.n_modes, inst.N, inst.K), np.float32)
+        self._check(self._lib.esdp_expected_value(self._ctx, asset, t, self._ptr(out),
+                                                  _stream(stream)))
+        return out
+
+    def bid_curves(self, asset: int, t0: int, t1: int, n_bp=None, idx=None, slope=None,
+                   stream=None):
+        inst = self.instances[asset]
+        n = t1 - t0
+        if n_bp is None:
+            assert not self.device
+            n_bp = np.empty((n, inst.n_modes, inst.K), np.int32)
+            idx = np.empty((n, inst.n_modes, inst.K, inst.N), np.int32)
+            slope = np.empty((n, inst.n_modes, inst.K, inst.N), np.float32)
+        p = (lambda a, d: _dev_ptr(a)) if self.device else _host_ptr
+        self._check(self._lib.esdp_bid_curves(self._ctx, asset, t0, t1, p(n_bp, np.int32),
+                                              p(idx, np.int32), p(slope, np.float32),
+                                              _stream(stream)))
+        return n_bp, idx, slope
+
+    def grad(self, asset: int, mu0, J=None, d_price=None, d_trans=None, d_eta=None, stream=None):
+        inst = self.instances[asset]
+        if not self.device:
+            mu0 = np.ascontiguousarray(mu0, dtype=np.float32)
+            J = np.zeros(1, np.float64) if J is None else J
+            d_price = np.zeros((inst.T, inst.K), np.float32) if d_price is None else d_price
+            d_trans = (np.zeros((inst.T, inst.K, inst.K), np.float32) if d_trans is None
+                       else d_trans)
+            d_eta = np.zeros(2, np.float64) if d_eta is None else d_eta
+            ptr = lambda a, dt: _host_ptr(a, dt)
+        else:
+            ptr = lambda a, dt: _dev_ptr(a)
+        self._check(self._lib.esdp_grad(self._ctx, asset, ptr(mu0, np.float32),
+                                        ptr(J, np.float64), ptr(d_price, np.float32),
+                                        ptr(d_trans, np.float32), ptr(d_eta, np.float64),
+                                        _stream(stream)))
+        return J, d_price, d_trans, d_eta
+
+    def autotune(self, stream=None):
+        self._check(self._lib.esdp_autotune(self._ctx, _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        return int(self._lib.esdp_status(self._ctx, _stream(stream)))
+
+    def launch_info(self) -> dict:
+        vals = [ctypes.c_int32() for _ in range(6)]
+        self._check(self._lib.esdp_launch_info(self._ctx, *[ctypes.byref(v) for v in vals]))
+        keys = ["grid", "block", "items", "rows_per_tile", "parts", "rows_per_thread"]
+        return {k: v.value for k, v in zip(keys, vals)}

@@ -1,0 +1,419 @@
+"""GPU (CUDA library, through the C ABI) against the FP64 oracle.
+
+Bars (stated for the method):
+  * values: max |V_gpu - V_oracle| <= 1e-5 * max |V_1 oracle|;
+  * policies: identical wherever the oracle's top-two action gap is at least
+    1e-6 * max |V_1| (near-ties may resolve either way in float32);
+  * bid-curve vertices: bit-exact against the oracle envelope run on the
+    GPU's own float32 EV; slopes within float32 rounding;
+  * gradients: max |g_gpu - g_oracle| <= 1e-4 * max |g_oracle| per tensor.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2511_15629_b300 import build as B
+from paper_2511_15629_b300 import esdp as E
+from paper_2511_15629_b300 import instances as I
+
+pytestmark = pytest.mark.gpu
+NTHREADS = max(1, len(os.sched_getaffinity(0)))
+VTOL = 1e-5
+GAPTOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    E.load_library()
+
+
+def _scale(V1):
+    return max(float(np.abs(V1).max()), 1e-12)
+
+
+def assert_values(gpu, ref, scale, what="V"):
+    err = float(np.abs(gpu.astype(np.float64) - ref).max()) / scale
+    assert err <= VTOL, f"{what}: max rel error {err:.3e} > {VTOL}"
+    return err
+
+
+def assert_policy(gpu, ref, gap, scale, what="policy"):
+    decided = gap >= GAPTOL * scale
+    bad = (gpu.astype(np.int64) != ref.astype(np.int64)) & decided
+    assert not bad.any(), f"{what}: {int(bad.sum())} mismatches outside near-ties"
+    # where the oracle saw a near-tie the GPU must still pick a maximiser
+    return int(((gpu != ref) & ~decided).sum())
+
+
+def solve_gpu(inst, keep_ev=False):
+    s = E.Solver([inst], keep_ev=keep_ev)
+    V1 = s.solve_instances()[0]
+    return s, V1
+
+
+def gpu_policies(s, inst):
+    return np.stack([s.policy(0, t) for t in range(1, inst.T + 1)])
+
+
+def full_check(inst, keep_ev=False, check_policy=True):
+    s, V1 = solve_gpu(inst, keep_ev=keep_ev)
+    r = O.solve(inst, keep_EV=keep_ev, nthreads=NTHREADS)
+    scale = _scale(r["V1"])
+    assert_values(V1, r["V1"], scale)
+    if check_policy and inst.policy_bytes and not inst.ckpt_every:
+        assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale)
+    if keep_ev:
+        ev = np.stack([s.expected_value(0, t) for t in range(1, inst.T + 1)])
+        assert_values(ev, r["EV"], scale, "EV")
+    return s, r
+
+
+# ----------------------------------------------------------------- sweep
+
+def test_config1_parity():
+    full_check(I.config1(), keep_ev=True)
+
+
+RANDOM_CASES = [
+    # T, N, K, D_dis, D_chg, modes, seed, cost
+    (5, 2, 1, 1, 0, 1, 1, "linear"),        # smallest grid
+    (7, 37, 3, 5, 2, 1, 2, "nonconvex"),    # ragged, asymmetric band
+    (6, 300, 33, 20, 17, 1, 3, "linear"),   # K not a multiple of the warp
+    (4, 129, 8, 64, 64, 2, 4, "nonconvex"), # band wider than a tile, two modes
+    (9, 50, 1, 49, 49, 1, 5, "linear"),     # band spans the whole grid
+    (3, 1000, 2, 0, 0, 1, 6, "zero"),       # idle only
+    (5, 64, 7, 0, 9, 2, 7, "linear"),       # charge-only band with modes
+    (5, 64, 7, 9, 0, 2, 8, "linear"),       # discharge-only band with modes
+    (12, 777, 16, 33, 31, 2, 9, "nonconvex"),
+    (2, 5001, 5, 100, 100, 1, 10, "linear"),
+]
+
+
+@pytest.mark.parametrize("case", RANDOM_CASES, ids=[f"T{c[0]}N{c[1]}K{c[2]}D{c[3]}-{c[4]}M{c[5]}"
+                                                     for c in RANDOM_CASES])
+def test_random_shapes_parity(case):
+    T, N, K, Dd, Dc, M, seed, cost = case
+    inst = I.random_instance(seed, T, N, K, Dd, Dc, M, neg_prob=0.25, cost=cost,
+                             switch_cost=4.0)
+    full_check(inst, keep_ev=True)
+
+
+def test_ties_resolve_to_smallest_action():
+    inst = I.random_instance(11, 4, 40, 3, 6, 6, 1, cost="zero", terminal="zero")
+    inst.price[:] = 0
+    s, V1 = solve_gpu(inst)
+    pol = gpu_policies(s, inst)
+    assert np.all(V1 == 0)
+    for si in range(inst.N):
+        assert np.all(pol[:, 0, si, :] == max(0, inst.D_dis - si))
+
+
+def test_integer_prices_exact_ties():
+    """Integer prices and a linear terminal give many exact float ties; the
+    GPU must still return the smallest maximiser of its own float values."""
+    inst = I.random_instance(12, 6, 90, 4, 7, 7, 2, integer_prices=True, cost="zero",
+                             terminal="linear", eta=(1.0, 1.0), s_max=90 * 0.25)
+    s, r = full_check(inst, keep_ev=True)
+
+
+def test_config2_parity_with_modes():
+    full_check(I.config2(), keep_ev=True)
+
+
+def test_config5_values_int16_checkpointed():
+    inst = I.config5()
+    s, V1 = solve_gpu(inst)
+    r = O.solve(inst, nthreads=NTHREADS, keep_policy=False)
+    assert_values(V1, r["V1"], _scale(r["V1"]))
+    with pytest.raises(E.EsdpError) as ei:
+        s.policy(0, 1)              # checkpointed: no full policy kept
+    assert ei.value.code == E.ESDP_ESTATE
+
+
+def test_int16_full_policy_matches_int32():
+    a = I.random_instance(13, 8, 200, 6, 12, 12, 2)
+    b = I.random_instance(13, 8, 200, 6, 12, 12, 2)
+    b.policy_bytes = 2
+    sa, Va = solve_gpu(a)
+    sb, Vb = solve_gpu(b)
+    np.testing.assert_array_equal(Va, Vb)
+    np.testing.assert_array_equal(gpu_policies(sa, a), gpu_policies(sb, b).astype(np.int32))
+
+
+def _c3_last(nstages):
+    inst = I.config3()
+    return I.Instance("config3_tail", nstages, inst.N, inst.K, inst.A, inst.D_dis, inst.D_chg, 1,
+                      inst.s_max, inst.tau, inst.eta_c, inst.eta_d, 0.0,
+                      inst.price[-nstages:].copy(), inst.trans[-nstages:].copy(), inst.cost,
+                      inst.terminal, s0=inst.s0)
+
+
+def test_config3_tail_full_parity():
+    """Full-width C3 stages (N=5001, K=64, A=201) over the last 12 stages."""
+    full_check(_c3_last(12), keep_ev=True)
+
+
+def test_config3_full_horizon_sampled_stages():
+    """The C3 sweep in its benchmark launch shape (all 2016 stages, keep EV).
+    Each sampled stage is checked against the oracle's Bellman step taken
+    from the GPU's own EV_t; V_1 against the full FP64 oracle."""
+    inst = I.config3()
+    s = E.Solver([inst], keep_ev=True)
+    V1 = s.solve_instances()[0]
+    for t in (inst.T, 1500, 700, 2):
+        ev_t = s.expected_value(0, t).astype(np.float64)
+        ev_prev = s.expected_value(0, t - 1).astype(np.float64)
+        r1 = _bellman_from_ev(inst, t, ev_t)
+        Vt, pol, gap = r1
+        scale = float(np.abs(Vt).max())
+        P = inst.trans[t - 2].astype(np.float64)
+        np.testing.assert_array_less(np.abs(Vt @ P.T - ev_prev).max() / scale, VTOL)
+        pg = s.policy(0, t)[0]
+        assert_policy(pg, pol, gap, scale, f"policy t={t}")
+    r = O.solve(inst, nthreads=NTHREADS, keep_policy=False)
+    assert_values(V1, r["V1"], _scale(r["V1"]))
+
+
+def _bellman_from_ev(inst, t, ev):
+    """Oracle Bellman step of stage t (eq. 5) from a given EV_t [1,N,K]."""
+    tmp = I.Instance("one", 1, inst.N, inst.K, inst.A, inst.D_dis, inst.D_chg, 1, inst.s_max,
+                     inst.tau, inst.eta_c, inst.eta_d, 0.0, inst.price[t - 1:t].copy(),
+                     np.eye(inst.K, dtype=np.float32)[None], inst.cost,
+                     np.zeros((1, inst.N, inst.K), np.float32))
+    # identity transition: EV_1 = V_2 = terminal, so pass ev as the terminal
+    r = O.solve(tmp, terminal=ev, nthreads=NTHREADS)
+    return r["V1"][0], r["policy"][0, 0], r["gap"][0, 0]
+
+
+# ------------------------------------------------------------ bid curves
+
+@pytest.mark.parametrize("which", ["config2", "random"])
+def test_bid_curves_bit_exact(which):
+    inst = I.config2() if which == "config2" else I.random_instance(21, 9, 400, 6, 25, 30, 1,
+                                                                     neg_prob=0.4,
+                                                                     cost="nonconvex")
+    s, V1 = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, slope = s.bid_curves(0, 1, inst.T + 1)
+    ev = np.stack([s.expected_value(0, t) for t in range(1, inst.T + 1)])
+    ref_n, ref_idx, ref_slope = O.bid_curves(inst, ev)
+    np.testing.assert_array_equal(n_bp, ref_n)
+    for t in range(inst.T):
+        for m in range(inst.n_modes):
+            for k in range(inst.K):
+                n = n_bp[t, m, k]
+                np.testing.assert_array_equal(idx[t, m, k, :n], ref_idx[t, m, k, :n])
+                np.testing.assert_allclose(slope[t, m, k, :n - 1], ref_slope[t, m, k, :n - 1],
+                                           rtol=1e-6, atol=1e-6)
+                # monotone bids: strictly decreasing in double, and no float32
+                # rounding can reverse the order
+                assert np.all(np.diff(ref_slope[t, m, k, :n - 1]) < 0)
+                assert np.all(np.diff(slope[t, m, k, :n - 1]) <= 0)
+
+
+def test_bid_curves_against_fp64_envelope():
+    """Against the envelope of the oracle's FP64 EV: vertices may differ only
+    where a vertex is nearly collinear with its neighbours."""
+    inst = I.config2()
+    s, V1 = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, slope = s.bid_curves(0, 1, inst.T + 1)
+    r = O.solve(inst, keep_EV=True, nthreads=NTHREADS, keep_policy=False)
+    ref_n, ref_idx, _ = O.bid_curves(inst, r["EV"])
+    same = 0
+    for t in range(inst.T):
+        for m in range(inst.n_modes):
+            for k in range(inst.K):
+                a = idx[t, m, k, :n_bp[t, m, k]]
+                b = ref_idx[t, m, k, :ref_n[t, m, k]]
+                if len(a) == len(b) and np.array_equal(a, b):
+                    same += 1
+                    continue
+                # envelopes agree to float32 accuracy even where vertices differ
+                y = r["EV"][t, m, :, k]
+                ea = np.interp(np.arange(inst.N), a, y[a])
+                eb = np.interp(np.arange(inst.N), b, y[b])
+                assert np.abs(ea - eb).max() <= 1e-6 * np.abs(y).max() + 1e-9
+    total = inst.T * inst.n_modes * inst.K
+    print(f"identical vertex sets vs the FP64-EV envelope: {same}/{total}")
+    assert same >= 0.5 * total
+
+
+# ------------------------------------------------------------- gradients
+
+def _gpu_full_policy(inst):
+    """The GPU's own stored argmax decisions for every stage (same values as a
+    checkpointed solve of the instance: the sweep is deterministic)."""
+    import copy
+    full = copy.copy(inst)
+    full.ckpt_every = 0
+    s, _ = solve_gpu(full)
+    return gpu_policies(s, full).astype(np.int32)
+
+
+def _grad_check(inst, tie_free):
+    s, V1 = solve_gpu(inst)
+    J, dp, dt, de = s.grad(0, inst.mu0)
+    r = O.solve(inst, keep_V=True, nthreads=NTHREADS)
+    scale = _scale(r["V1"])
+    pol = _gpu_full_policy(inst)
+    n_near_tie = assert_policy(pol, r["policy"], r["gap"], scale)
+    # the bar: FP64 occupancy pass under the same decisions as the GPU
+    occ = O.occupancy(inst, pol, r["V"])
+    assert J[0] == pytest.approx(occ["J"], rel=VTOL)
+    checks = (("d_price", dp, "d_price"), ("d_trans", dt, "d_trans"),
+              ("d_eta_c", de[:1], "d_eta_c"), ("d_eta_d", de[1:], "d_eta_d"))
+    for name, g, key in checks:
+        ref = np.atleast_1d(occ[key])
+        err = np.abs(g.astype(np.float64).reshape(ref.shape) - ref).max() / max(np.abs(ref).max(), 1e-12)
+        assert err <= 1e-4, f"{name}: rel error {err:.3e}"
+    if tie_free:
+        # no near-ties: the oracle's own decisions give the same gradient
+        assert n_near_tie == 0
+        occ2 = O.occupancy(inst, r["policy"], r["V"])
+        for name, g, key in checks:
+            ref = np.atleast_1d(occ2[key])
+            err = np.abs(g.astype(np.float64).reshape(ref.shape) - ref).max() / max(np.abs(ref).max(), 1e-12)
+            assert err <= 1e-4, f"{name} (oracle decisions): rel error {err:.3e}"
+    return n_near_tie
+
+
+def test_gradient_small_tie_free():
+    inst = I.random_instance(53, 6, 25, 3, 3, 3, 1, neg_prob=0.2, cost="linear")
+    inst.s0 = 12
+    _grad_check(inst, tie_free=True)
+
+
+def test_gradient_modes_checkpointed():
+    inst = I.random_instance(54, 40, 120, 5, 9, 9, 2, neg_prob=0.2, switch_cost=3.0)
+    inst.s0 = 60
+    inst.ckpt_every = 7
+    inst.policy_bytes = 2
+    _grad_check(inst, tie_free=False)
+
+
+def test_gradient_config5():
+    n = _grad_check(I.config5(), tie_free=False)
+    print(f"config5: {n} near-tie decisions differ from the FP64 oracle's")
+
+
+# --------------------------------------------------------------- batching
+
+def test_batched_equals_solo_and_oracle():
+    assets = [I.random_instance(60 + j, 10, n, k, d1, d2, m, neg_prob=0.2)
+              for j, (n, k, d1, d2, m) in enumerate([(300, 8, 20, 20, 1), (77, 3, 5, 9, 2),
+                                                     (1001, 12, 40, 40, 1), (2, 1, 1, 1, 1),
+                                                     (450, 40, 60, 50, 1), (130, 5, 3, 3, 2)])]
+    s = E.Solver(assets)
+    V1s = s.solve_instances()
+    for inst, V1 in zip(assets, V1s):
+        _, solo = solve_gpu(inst)
+        np.testing.assert_array_equal(V1, solo)
+        r = O.solve(inst, nthreads=NTHREADS, keep_policy=False)
+        assert_values(V1, r["V1"], _scale(r["V1"]))
+
+
+def test_config4_subset_truncated_horizon():
+    """16 portfolio assets with their full N, K, A on a 24-stage horizon."""
+    assets = []
+    for j in range(16):
+        a = I.config4_asset(j)
+        a.T = 24
+        a.price = np.ascontiguousarray(a.price[:24])
+        a.trans = np.ascontiguousarray(a.trans[:24])
+        assets.append(a)
+    s = E.Solver(assets)
+    for inst, V1 in zip(assets, s.solve_instances()):
+        r = O.solve(inst, nthreads=NTHREADS, keep_policy=False)
+        assert_values(V1, r["V1"], _scale(r["V1"]), inst.name)
+
+
+# ---------------------------------------------------- device mode / errors
+
+def test_device_pointers_and_graph_capture():
+    import torch
+    inst = I.random_instance(70, 20, 500, 10, 30, 30, 2)
+    cat = E.concat_inputs([inst])
+    dev = {k: torch.from_numpy(v).cuda() for k, v in cat.items()}
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s.solve(dev["price"], dev["trans"], dev["cost"], dev["terminal"], V1, stream=st)
+    st.synchronize()
+    assert s.status(stream=st) == 0
+    _, ref = solve_gpu(inst)
+    np.testing.assert_array_equal(V1.cpu().numpy().reshape(ref.shape), ref)
+    # capture the solve in a CUDA graph and replay it on new prices
+    g = torch.cuda.CUDAGraph()
+    V2 = torch.zeros_like(V1)
+    with torch.cuda.graph(g, stream=st):
+        s.solve(dev["price"], dev["trans"], dev["cost"], dev["terminal"], V2,
+                stream=torch.cuda.current_stream())
+    dev["price"].mul_(1.5)
+    g.replay()
+    torch.cuda.synchronize()
+    inst2 = I.random_instance(70, 20, 500, 10, 30, 30, 2)
+    inst2.price = (inst2.price * np.float32(1.5)).astype(np.float32)
+    _, ref2 = solve_gpu(inst2)
+    np.testing.assert_array_equal(V2.cpu().numpy().reshape(ref2.shape), ref2)
+
+
+def test_bad_inputs_rejected():
+    inst = I.random_instance(71, 4, 50, 3, 4, 4, 1)
+    s = E.Solver([inst])
+    cat = E.concat_inputs([inst])
+    with pytest.raises(E.EsdpError) as ei:
+        s.policy(0, 1)
+    assert ei.value.code == E.ESDP_ESTATE
+    bad = dict(cat)
+    bad["price"] = cat["price"].copy()
+    bad["price"][3] = np.nan
+    with pytest.raises(E.EsdpError) as ei:
+        s.solve(bad["price"], bad["trans"], bad["cost"], bad["terminal"])
+    assert ei.value.code == E.ESDP_EINVAL
+    bad = dict(cat)
+    bad["trans"] = cat["trans"].copy()
+    bad["trans"][5] = -0.1
+    with pytest.raises(E.EsdpError) as ei:
+        s.solve(bad["price"], bad["trans"], bad["cost"], bad["terminal"])
+    assert ei.value.code == E.ESDP_EINVAL
+    with pytest.raises(E.EsdpError) as ei:
+        s.bid_curves(0, 1, 2)
+    assert ei.value.code in (E.ESDP_ESTATE,)
+    s.solve(cat["price"], cat["trans"], cat["cost"], cat["terminal"])  # still usable
+    with pytest.raises(E.EsdpError) as ei:
+        s.policy(0, inst.T + 1)
+    assert ei.value.code == E.ESDP_EINVAL
+
+
+def test_bounded_wait_times_out_and_context_recovers(monkeypatch):
+    """Every neighbour wait is made to wait for a flag value nothing
+    publishes; the bounded spin must give up, report ESDP_ETIMEOUT through
+    the status word, and leave the context usable."""
+    monkeypatch.setenv("ESDP_TIMEOUT_MS", "300")
+    inst = I.random_instance(72, 6, 400, 4, 10, 10, 1)
+    s = E.Solver([inst])
+    cat = E.concat_inputs([inst])
+    monkeypatch.setenv("ESDP_INJECT_STALL", "1")
+    with pytest.raises(E.EsdpError) as ei:
+        s.solve(cat["price"], cat["trans"], cat["cost"], cat["terminal"])
+    assert ei.value.code == E.ESDP_ETIMEOUT
+    monkeypatch.delenv("ESDP_INJECT_STALL")
+    V1 = np.empty(inst.N * inst.K, np.float32)
+    s.solve(cat["price"], cat["trans"], cat["cost"], cat["terminal"], V1)
+    r = O.solve(inst, keep_policy=False)
+    assert_values(V1.reshape(1, inst.N, inst.K), r["V1"], _scale(r["V1"]))
+
+
+def test_autotune_keeps_results():
+    inst = I.random_instance(73, 12, 900, 16, 40, 40, 1)
+    s, V1 = solve_gpu(inst)
+    s.autotune()
+    V1b = s.solve_instances()[0]
+    np.testing.assert_array_equal(V1, V1b)
+    info = s.launch_info()
+    assert info["grid"] >= 1 and info["rows_per_thread"] in (4, 8, 12, 16)
