@@ -141,6 +141,39 @@ int esdp_status(esdp_ctx* ctx, void* stream);
 int esdp_launch_info(const esdp_ctx* ctx, int32_t* grid, int32_t* block, int32_t* items,
                      int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread);
 
+/* Allocation-free solve of one asset.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for example a
+ * plug-in running inside an application that owns the device memory pool
+ * through its own caching allocator, a process under a hard device-memory
+ * quota, or code on a latency-critical path where an allocation could
+ * stall.  It runs the same persistent sweep as esdp_solve (eq. 5-6,
+ * Algorithm 1) but needs no context and allocates nothing: its workspace
+ * (EV halo buffers, neighbour flags, status word, stage levels, launch plan)
+ * is one file-scope device array of ESDP_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library reserves until the process exits.
+ *   asset: description as for esdp_create (policy_bytes 2 or 4 when `policy`
+ *          is given; ckpt_every is ignored);
+ *   price [T*K], trans [T*K*K], cost [A], terminal [n_modes*N*K]: device
+ *          pointers, read only;  V1 [n_modes*N*K]: device pointer, written;
+ *   policy: NULL, or a device buffer of T*n_modes*N*K int32/int16 entries;
+ *   stream: cudaStream_t (NULL = legacy default stream);
+ *   err/err_len: optional buffer for a message (always NUL-terminated).
+ * The call is queued on `stream` and returns when it has finished; the
+ * result code includes the device status word (ESDP_ETIMEOUT etc.).
+ * Limits: the asset must fit the workspace, about 2*n_modes*N*K floats of EV
+ * plus 2*T*K doubles of per-stage data (N*K up to roughly 1.9 million for one
+ * mode and T = 288), and at most 2048 tiles; larger assets are rejected with
+ * ESDP_EINVAL and a message that states the bytes needed.
+ * The first call on a device looks up the workspace address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one
+ * workspace: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+#define ESDP_NOALLOC_SCRATCH_BYTES (16u << 20)
+int esdp_solve_noalloc(const esdp_asset* asset, const float* price, const float* trans,
+                       const float* cost, const float* terminal, float* V1, void* policy,
+                       void* stream, char* err, int32_t err_len);
+
 void esdp_destroy(esdp_ctx* ctx);
 const char* esdp_last_error(const esdp_ctx* ctx);
 int esdp_version(void);

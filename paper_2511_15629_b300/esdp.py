@@ -268,3 +268,21 @@ class Solver:
         self._check(self._lib.esdp_launch_info(self._ctx, *[ctypes.byref(v) for v in vals]))
         keys = ["grid", "block", "items", "rows_per_tile", "parts", "rows_per_thread"]
         return {k: v.value for k, v in zip(keys, vals)}
+
+
+def solve_noalloc(inst, price, trans, cost, terminal, V1, policy=None, stream=None) -> None:
+    """Allocation-free solve of one asset (esdp_solve_noalloc): for callers
+    that cannot allocate device memory.  All arrays are device tensors (or
+    raw device addresses) that the caller owns; the library's fixed device
+    workspace is shared by every call on the device, so overlapping calls
+    must be serialised.  Blocks until the solve has finished."""
+    lib = load_library()
+    fn = lib.esdp_solve_noalloc
+    fn.argtypes = [ctypes.POINTER(Asset)] + [ctypes.c_void_p] * 8 + [ctypes.c_int32]
+    fn.restype = ctypes.c_int
+    a = asset_from_instance(inst)
+    err = ctypes.create_string_buffer(512)
+    rc = fn(ctypes.byref(a), _dev_ptr(price), _dev_ptr(trans), _dev_ptr(cost), _dev_ptr(terminal),
+            _dev_ptr(V1), _dev_ptr(policy), _stream(stream), err, len(err))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, err.value.decode())
