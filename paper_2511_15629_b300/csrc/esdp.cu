@@ -40,7 +40,7 @@ struct Plan {
   std::vector<int> cta_items;
   int n_steps = 0;
   int n_flags = 0;
-  int sm_E = 0, sm_R = 0, sm_V = 0, sm_P = 0, sm_X = 0;
+  int sm_E = 0, sm_R = 0, sm_C = 0, sm_V = 0, sm_P = 0, sm_X = 0;
   AssetDev* d_assets = nullptr;
   WorkItem* d_items = nullptr;
   int* d_cta = nullptr;
@@ -170,17 +170,8 @@ struct AssetChoice {
   int nb, parts, W, n_tiles, rows, rs;
 };
 
-size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R, int* E, int* Rt, int* V,
-                 int* P, int* X) {
-  const int M = a.n_modes, K = a.K;
-  *E = M * ch.rows * K;
-  *Rt = M * K * ch.rs;
-  *V = M * ch.W * K;
-  *P = K * K;
-  *X = 2 * ch.parts * M * ch.W * K;
-  (void)R;
-  auto al = [](int x) { return (x + 3) / 4 * 4; };
-  return (size_t)(al(*E) + al(*Rt) + al(*V) + al(*P) + al(*X)) * sizeof(float);
+size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R) {
+  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R, ch.parts).bytes;
 }
 
 int n_chunks_min(const esdp_asset& a, int R) {
@@ -211,9 +202,8 @@ bool choose_asset(const esdp_asset& a, int R, int block, double cta_share, Asset
     const int dmax = std::max(a.D_dis, a.D_chg);
     const int nw = 2 * ((dmax + ch.W - 1) / ch.W) + 1;
     if (nw + 1 > block) continue;  // one thread per neighbour wait + the reference tile
-    int e, rt, v, p, x;
-    while (smem_need(a, ch, R, &e, &rt, &v, &p, &x) > kSmemLimit && ch.parts > 1) --ch.parts;
-    if (smem_need(a, ch, R, &e, &rt, &v, &p, &x) > kSmemLimit) continue;
+    while (smem_need(a, ch, R) > kSmemLimit && ch.parts > 1) --ch.parts;
+    if (smem_need(a, ch, R) > kSmemLimit) continue;
     *out = ch;
     return true;
   }
@@ -243,7 +233,8 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
   }
   std::vector<AssetChoice> ch(ids.size());
   int flag_base = 0;
-  int sm_E = 0, sm_R = 0, sm_V = 0, sm_P = 0, sm_X = 0;
+  // the launch's carve-up must hold every asset: take the largest region sizes
+  long long need_E = 0, need_R = 0, need_C = 0, need_V = 0, need_P = 0, need_X = 0;
   for (size_t j = 0; j < ids.size(); ++j) {
     const esdp_asset& a = c->assets[ids[j]];
     const double work = (double)a.n_modes * a.N * a.K * a.A;
@@ -252,13 +243,16 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
       return fail(c, ESDP_EINVAL,
                   "asset %d (K=%d, modes=%d, A=%d) does not fit a %d-thread tile in shared memory",
                   ids[j], a.K, a.n_modes, a.A, block);
-    int e, rt, v, p, x;
-    smem_need(a, ch[j], R, &e, &rt, &v, &p, &x);
-    sm_E = std::max(sm_E, e);
-    sm_R = std::max(sm_R, rt);
-    sm_V = std::max(sm_V, v);
-    sm_P = std::max(sm_P, p);
-    sm_X = std::max(sm_X, x);
+    {
+      const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R, ch[j].parts);
+      const long long endX = (long long)(L.bytes / sizeof(float));
+      need_E = std::max<long long>(need_E, L.Rt - L.E);
+      need_R = std::max<long long>(need_R, L.C - L.Rt);
+      need_C = std::max<long long>(need_C, L.V - L.C);
+      need_V = std::max<long long>(need_V, L.P - L.V);
+      need_P = std::max<long long>(need_P, L.X - L.P);
+      need_X = std::max<long long>(need_X, endX - L.X);
+    }
     AssetDev d{};
     d.T = a.T; d.N = a.N; d.K = a.K; d.A = a.A; d.D_dis = a.D_dis; d.D_chg = a.D_chg;
     d.M = a.n_modes;
@@ -298,13 +292,13 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     flag_base += d.n_tiles;
   }
   plan->n_flags = flag_base;
-  auto al = [](int x) { return (x + 3) / 4 * 4; };
   plan->sm_E = 0;
-  plan->sm_R = al(sm_E);
-  plan->sm_V = plan->sm_R + al(sm_R);
-  plan->sm_P = plan->sm_V + al(sm_V);
-  plan->sm_X = plan->sm_P + al(sm_P);
-  plan->shape.smem = (size_t)(plan->sm_X + al(sm_X)) * sizeof(float);
+  plan->sm_R = (int)need_E;
+  plan->sm_C = plan->sm_R + (int)need_R;
+  plan->sm_V = plan->sm_C + (int)need_C;
+  plan->sm_P = plan->sm_V + (int)need_V;
+  plan->sm_X = plan->sm_P + (int)need_P;
+  plan->shape.smem = (size_t)(plan->sm_X + need_X) * sizeof(float);
   if (plan->shape.smem > kSmemLimit)
     return fail(c, ESDP_EINVAL, "shared memory plan of %zu bytes exceeds the limit",
                 plan->shape.smem);
@@ -407,6 +401,7 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
   sp.item_c = p->d_item_c;
   sp.sm_E = p->sm_E;
   sp.sm_R = p->sm_R;
+  sp.sm_C = p->sm_C;
   sp.sm_V = p->sm_V;
   sp.sm_P = p->sm_P;
   sp.sm_X = p->sm_X;

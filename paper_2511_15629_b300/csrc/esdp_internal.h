@@ -68,9 +68,29 @@ struct SweepParams {
   unsigned long long timeout_ns;
   int wait_extra;            // 0; > 0 only in the stall test: waits for a value nobody publishes
   double* item_c;            // [items] running level c of each work item
-  // shared-memory carve-up (floats)
-  int sm_E, sm_R, sm_V, sm_P, sm_X;
+  // shared-memory carve-up (floats), see sweep_smem_layout
+  int sm_E, sm_R, sm_C, sm_V, sm_P, sm_X;
 };
+
+// Shared-memory carve-up of the sweep kernel (offsets in floats, every region
+// 128-byte aligned so that bulk copies and float4 accesses are aligned).
+struct SweepSmem {
+  int E, Rt, C, V, P, X;
+  size_t bytes;
+};
+inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R, int parts) {
+  auto al = [](long long x) { return (int)((x + 31) / 32 * 32); };
+  const int rows = W + A + R, rs = (A + 2 * R) | 1, Kp4 = (K + 3) & ~3;
+  SweepSmem s;
+  s.E = 0;
+  s.Rt = s.E + al((long long)M * rows * K);
+  s.C = s.Rt + al((long long)M * K * rs);
+  s.V = s.C + al(2LL * M * rs);
+  s.P = s.V + al((long long)M * W * (K + 1));
+  s.X = s.P + al((long long)K * Kp4);
+  s.bytes = (size_t)(s.X + al(2LL * parts * M * W * K)) * sizeof(float);
+  return s;
+}
 
 // Launch shape of one sweep.
 struct SweepShape {

@@ -111,8 +111,7 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   if (nb_max < 1) return msg(err, err_len, ESDP_EINVAL, "K * n_modes exceeds 512");
   int nb = std::max(1, std::min(nb_max, (a.N + n_sm * R - 1) / (n_sm * R)));
   int W = 0, tiles = 0, parts = 1, rows = 0, rs = 0;
-  size_t smem = 0;
-  int sm_R = 0, sm_V = 0, sm_P = 0, sm_X = 0;
+  SweepSmem L{};
   for (; nb >= 1; --nb) {
     W = nb * R;
     tiles = (a.N + W - 1) / W;
@@ -122,18 +121,10 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
     if (2 * reach + 2 > block) continue;
     parts = std::max(1, std::min(block / (KM * nb), chunks_min(a, R) / 2));
     for (; parts >= 1; --parts) {
-      auto al = [](size_t x) { return (x + 3) / 4 * 4; };
-      const size_t E = al((size_t)M * rows * K), Rt = al((size_t)M * K * rs),
-                   V = al((size_t)M * W * K), P = al((size_t)K * K),
-                   X = al((size_t)2 * parts * M * W * K);
-      sm_R = (int)E;
-      sm_V = (int)(E + Rt);
-      sm_P = (int)(E + Rt + V);
-      sm_X = (int)(E + Rt + V + P);
-      smem = (E + Rt + V + P + X) * sizeof(float);
-      if (smem <= kSmemLimit) break;
+      L = sweep_smem_layout(M, K, W, a.A, R, parts);
+      if (L.bytes <= kSmemLimit) break;
     }
-    if (parts >= 1 && smem <= kSmemLimit) break;
+    if (parts >= 1 && L.bytes <= kSmemLimit) break;
   }
   if (nb < 1) return msg(err, err_len, ESDP_EINVAL, "no launch shape fits shared memory");
   if (tiles > kNoAllocMaxItems) {
@@ -141,6 +132,7 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
              kNoAllocMaxItems);
     return msg(err, err_len, ESDP_EINVAL, buf);
   }
+  const size_t smem = L.bytes;
   const int per_sm = sweep_max_blocks_per_sm(R, block, smem);
   if (per_sm < 1) return msg(err, err_len, ESDP_ECUDA, "sweep kernel does not fit on an SM");
   const int grid = std::min(tiles, per_sm * n_sm);
@@ -242,11 +234,12 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   sp.timeout_ns = 5ull * 1000 * 1000 * 1000;
   sp.wait_extra = 0;
   sp.item_c = reinterpret_cast<double*>(S + o_itemc);
-  sp.sm_E = 0;
-  sp.sm_R = sm_R;
-  sp.sm_V = sm_V;
-  sp.sm_P = sm_P;
-  sp.sm_X = sm_X;
+  sp.sm_E = L.E;
+  sp.sm_R = L.Rt;
+  sp.sm_C = L.C;
+  sp.sm_V = L.V;
+  sp.sm_P = L.P;
+  sp.sm_X = L.X;
   SweepShape shape;
   shape.R = R;
   shape.block = block;

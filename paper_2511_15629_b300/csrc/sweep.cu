@@ -4,24 +4,32 @@
 // One cooperative launch runs every stage of every asset.  A work item is a
 // tile of W consecutive SoC rows of one asset with all K price states and
 // all modes.  Per stage t the item
-//   1. waits (bounded spin) until the tiles whose rows it reads, and the
-//      tiles that read its rows, have published EV_t;
-//   2. stages EV_t rows [s0 - D_dis, s1 + D_chg) of every mode in shared
-//      memory (out-of-grid rows = -inf: the infeasibility mask of Alg. 1);
-//   3. builds the payoff table r[m][k][a] = price[t][k] e_a - cost[a]
-//      (- switch cost) for its modes;
-//   4. runs the banded max-plus over the action band with a register window
-//      of R rows per thread and a chunked argmax (exact smallest index);
-//   5. writes V_t (shared) and the policy, then contracts
-//      EV_{t-1}[m][s][k] = sum_k2 P_{t-1}[k][k2] V_t[m][s][k2] for its own
-//      rows (a pointwise-in-s product, so no halo is recomputed) and
-//      publishes it with a release flag.
-// V therefore never leaves the SM: only EV_{t-1} goes to L2, where the
-// neighbouring tiles pick up their halos for stage t-1.
+//   0. prefetches what does not depend on other tiles (P_{t-1} transposed via
+//      cp.async, its prices and transition row sums);
+//   1. waits (bounded spin) until the tiles whose rows it reads, the tiles
+//      that read its rows and the tile holding the reference row have
+//      published EV_t;
+//   2. stages EV_t rows [s0 - D_dis, s1 + D_chg + R) of every mode in shared
+//      memory with TMA bulk copies (rows outside the grid are -inf: the
+//      infeasibility mask of Alg. 1), overlapped with building the payoff
+//      table r[m][k][a] = price[t][k] e_a - cost[a] (- switch cost);
+//   3. runs the banded max-plus: a thread owns R consecutive rows of one
+//      (m, k) and slides a register window of EV values over the action band
+//      (two evaluations per 3-input max), tracking the winning chunk of R
+//      actions and recovering the exact smallest maximiser afterwards;
+//   4. keeps V_t in shared memory, stores the policy, and contracts
+//      EV_{t-1}[m][s][k] = sum_k2 P_{t-1}[k][k2] V_t[m][s][k2] for its own rows
+//      (pointwise in s: no halo is recomputed), then publishes it.
+// V never leaves the SM; EV goes to L2 where neighbours pick up their halos.
+//
+// Float32 values are kept centred: V'_t = V_t - c_t with a scalar level
+// c_t = c_{t+1} + EV'_t[ref] carried in double (the same on every tile), and
+// the payoff of price state k absorbs c_{t+1} rowsum(P_t)[k] - c_t.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "../../include/esdp.h"
 #include "esdp_internal.h"
@@ -43,6 +51,74 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the bulk copies of this stage.  On expiry: report
+// ESDP_ETIMEOUT, give the copies one more bounded wait, and tell the caller to
+// abandon the launch.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, const SweepParams& p) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = now_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (now_ns() - t0 > p.timeout_ns) {
+      atomicCAS(p.status, 0, ESDP_ETIMEOUT);
+      t0 = now_ns();
+      while (!mbar_try_wait(bar, parity) && now_ns() - t0 <= p.timeout_ns) {
+      }
+      return false;
+    }
+  }
+  return true;
 }
 
 struct Seg {
@@ -75,34 +151,61 @@ __device__ __forceinline__ float* ev_ptr(const AssetDev& as, int t) {
   return as.ev_keep ? as.ev + (size_t)(t - 1) * mnk(as) : as.ev + (size_t)(t & 1) * mnk(as);
 }
 
-// Load P_t transposed: Ps[k2*K + k] = trans[t][k][k2].
-__device__ __forceinline__ void load_trans(const SweepParams& p, const AssetDev& as, int t,
-                                           float* Ps) {
-  const int K = as.K;
+// Issue the asynchronous load of P_t transposed: Ps[k2*Kp4 + k] = trans[t][k][k2].
+__device__ __forceinline__ void prefetch_trans(const SweepParams& p, const AssetDev& as, int t,
+                                               float* Ps) {
+  const int K = as.K, Kp4 = (K + 3) & ~3;
   const float* P = p.trans + as.off_trans + (size_t)(t - 1) * K * K;
   for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
-    const int k = i / K, k2 = i - k * K;
-    Ps[k2 * K + k] = __ldg(P + i);
+    const int k2 = i / K, k = i - k2 * K;
+    cp_async4(Ps + k2 * Kp4 + k, P + (size_t)k * K + k2);
   }
 }
 
-// EV rows of the item from the V tile in shared memory (eq. 6).  `te` is
-// the stage of the EV being produced; the reference entry is also kept in
-// its own per-stage slot.
+// EV rows of the item (eq. 6) from V' in shared memory (row stride K+1):
+// each thread forms 2 rows x 4 price states; the sum over k2 runs in
+// ascending order with one fma per term.  `te` is the stage of the EV being
+// produced; its reference entry also goes to its own per-stage slot.
 __device__ __forceinline__ void expectation(const AssetDev& as, const WorkItem& w, int te,
                                             const float* Ps, const float* Vs, float* dst) {
-  const int K = as.K, M = as.M, W = as.W, N = as.N;
+  const int K = as.K, M = as.M, W = as.W, N = as.N, Kv = K + 1, Kp4 = (K + 3) & ~3;
   const int Wt = w.s1 - w.s0;
-  const int total = M * Wt * K;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int k = i % K;
-    const int r = (i / K) % Wt;
-    const int m = i / (K * Wt);
-    const float* v = Vs + (size_t)(m * W + r) * K;
-    float acc = 0.f;
-    for (int k2 = 0; k2 < K; ++k2) acc = fmaf(Ps[k2 * K + k], v[k2], acc);
-    __stcg(dst + ((size_t)m * N + w.s0 + r) * K + k, acc);
-    if (m == 0 && k == 0 && w.s0 + r == as.ref_row) __stcg(as.ref_hist + te, acc);
+  const int G = (K + 3) >> 2;
+  const int n_rows = M * Wt;
+  const int units = ((n_rows + 1) >> 1) * G;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int g = u % G, rp = u / G;
+    const int L0 = 2 * rp, L1 = min(2 * rp + 1, n_rows - 1);
+    const int m0 = L0 / Wt, r0 = L0 - m0 * Wt;
+    const int m1 = L1 / Wt, r1 = L1 - m1 * Wt;
+    const float* v0 = Vs + (m0 * W + r0) * Kv;
+    const float* v1 = Vs + (m1 * W + r1) * Kv;
+    const float* pp = Ps + 4 * g;
+    float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k2 = 0; k2 < K; ++k2) {
+      const float4 q = *reinterpret_cast<const float4*>(pp + k2 * Kp4);
+      const float x0 = v0[k2], x1 = v1[k2];
+      a0[0] = fmaf(q.x, x0, a0[0]);
+      a0[1] = fmaf(q.y, x0, a0[1]);
+      a0[2] = fmaf(q.z, x0, a0[2]);
+      a0[3] = fmaf(q.w, x0, a0[3]);
+      a1[0] = fmaf(q.x, x1, a1[0]);
+      a1[1] = fmaf(q.y, x1, a1[1]);
+      a1[2] = fmaf(q.z, x1, a1[2]);
+      a1[3] = fmaf(q.w, x1, a1[3]);
+    }
+    float* d0 = dst + ((size_t)m0 * N + w.s0 + r0) * K + 4 * g;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * g + j < K) __stcg(d0 + j, a0[j]);
+    if (m0 == 0 && g == 0 && w.s0 + r0 == as.ref_row) __stcg(as.ref_hist + te, a0[0]);
+    if (2 * rp + 1 < n_rows) {
+      float* d1 = dst + ((size_t)m1 * N + w.s0 + r1) * K + 4 * g;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * g + j < K) __stcg(d1 + j, a1[j]);
+      if (m1 == 0 && g == 0 && w.s0 + r1 == as.ref_row) __stcg(as.ref_hist + te, a1[0]);
+    }
   }
 }
 
@@ -114,14 +217,15 @@ __device__ __forceinline__ void publish(int* flag, int v) {
   }
 }
 
-// Wait until every neighbour tile has published at least `need` EV arrays.
-// Returns false (uniformly over the CTA) if the launch is being abandoned.
+// Wait until every neighbour tile and the reference tile have published at
+// least `need` EV arrays; the thread that waits for the reference tile also
+// reads EV'_t[ref].  Returns false (uniformly over the CTA) if the launch is
+// being abandoned.
 __device__ bool wait_neighbours(const SweepParams& p, const AssetDev& as, const WorkItem& w,
-                                int need, int* s_abort) {
+                                int need, int t, int* s_abort, float* s_ref) {
   const int lo = max(0, w.tile + as.wait_lo);
   const int hi = min(as.n_tiles - 1, w.tile + as.wait_hi);
   const int n = hi - lo + 1;
-  // one more thread waits for the tile that holds the reference row
   if ((int)threadIdx.x <= n) {
     const int tile = (int)threadIdx.x < n ? lo + (int)threadIdx.x : as.ref_tile;
     const int* f = p.flags + as.flag_base + tile;
@@ -140,86 +244,133 @@ __device__ bool wait_neighbours(const SweepParams& p, const AssetDev& as, const 
         }
       }
     }
+    if ((int)threadIdx.x == n) *s_ref = __ldcg(as.ref_hist + t);
   }
-  __threadfence();
   __syncthreads();
   return *(volatile int*)s_abort == 0;
 }
 
-template <int R>
-__device__ void stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it, int t,
-                      float* Es, float* Rt, float* Vs, float* Ps, float* Xs, double* s_lvl,
-                      float* s_delta) {
-  const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const float NEG = -CUDART_INF_F;
+struct Smem {
+  float *Es, *Rt, *Ecol, *Ccol, *Vs, *Ps, *Xs;
+  double* lvl;     // [2]: c_{t+1}, c_t
+  float* lam;      // [K] prices of the stage
+  float* delta;    // [K] level correction of the stage
+  float* ref;      // EV'_t[ref]
+  int* abort;
+  uint64_t* bar;
+};
 
-  // 0. level of this stage: c_t = c_{t+1} + EV'_t[ref], the same double on
-  //    every tile of the asset; the payoff of price state k absorbs
-  //    c_{t+1} rho_t[k] - c_t so that the float values stay centred
+// One stage of one work item.  Returns false if the launch is abandoned.
+template <int R>
+__device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
+                           int g, const Smem& sm, uint32_t& parity) {
+  const int t = as.t_hi - g;
+  const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
+            nwarps = nth >> 5;
+  const float NEG = -CUDART_INF_F;
+  const bool tma = (K & 3) == 0;
+
+  // 0. prefetch the inputs of the stage
+  if (t > as.t_lo) prefetch_trans(p, as, t - 1, sm.Ps);
+  float lam_k = 0.f;
+  double rho_k = 0.0, c_next = 0.0;
+  if (tid < K) {
+    lam_k = __ldg(p.price + as.off_price + (size_t)(t - 1) * K + tid);
+    rho_k = __ldg(as.rho + (size_t)(t - 1) * K + tid);
+  }
+  if (tid == 0) c_next = p.item_c[it];
+
+  // 1. neighbours
+  if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
+
+  // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
+  const float* ev_t = ev_ptr(as, t);
+  const int g0row = w.s0 - as.D_dis;
+  const int lo = max(g0row, 0), hi = min(g0row + rows, N);
+  if (tma) {
+    if (tid == 0) {
+      asm volatile("fence.proxy.async;" ::: "memory");
+      const uint32_t bytes = (uint32_t)(hi - lo) * K * 4u;
+      mbar_expect_tx(sm.bar, bytes * M);
+      for (int m = 0; m < M; ++m)
+        bulk_load(sm.Es + ((size_t)m * rows + (lo - g0row)) * K, ev_t + ((size_t)m * N + lo) * K,
+                  bytes, sm.bar);
+    }
+  } else {
+    for (int m = 0; m < M; ++m) {
+      const float* src = ev_t + ((size_t)m * N + lo) * K;
+      float* dst = sm.Es + ((size_t)m * rows + (lo - g0row)) * K;
+      const int n = (hi - lo) * K;
+      for (int i = tid; i < n; i += nth) dst[i] = __ldcg(src + i);
+    }
+  }
+  {
+    const int below = (lo - g0row) * K, above0 = (hi - g0row) * K, total = rows * K;
+    for (int m = 0; m < M; ++m) {
+      float* e = sm.Es + (size_t)m * rows * K;
+      for (int i = tid; i < below; i += nth) e[i] = NEG;
+      for (int i = above0 + tid; i < total; i += nth) e[i] = NEG;
+    }
+  }
+  // level of the stage and the per-state correction of the payoffs
   if (tid == 0) {
-    const double c_next = p.item_c[it];
-    const double c_t = c_next + (double)__ldcg(as.ref_hist + t);
-    s_lvl[0] = c_next;
-    s_lvl[1] = c_t;
+    const double c_t = c_next + (double)*sm.ref;
+    sm.lvl[0] = c_next;
+    sm.lvl[1] = c_t;
     p.item_c[it] = c_t;
     if (w.tile == 0) as.off[t] = c_t;
   }
-  __syncthreads();
-  for (int k = tid; k < K; k += nth) {
-    const double cr = s_lvl[0] * as.rho[(size_t)(t - 1) * K + k];
-    s_delta[k] = (float)(cr - s_lvl[1]);
-    if (w.tile == 0) as.evoff[(size_t)(t - 1) * K + k] = cr;
-  }
-
-  // 1. EV_t tile with halo; rows outside the grid are infeasible (-inf)
+  // payoff columns of each mode: e_a and -(cost_a + switch), -inf padding
   {
-    const float* ev_t = ev_ptr(as, t);
-    const long long g0 = (long long)(w.s0 - as.D_dis) * K;
-    const long long lim = (long long)N * K;
-    const int total = rows * K;
-    for (int m = 0; m < M; ++m) {
-      const float* src = ev_t + (size_t)m * N * K;
-      float* dst = Es + (size_t)m * rows * K;
-      for (int i = tid; i < total; i += nth) {
-        const long long gi = g0 + i;
-        dst[i] = (gi >= 0 && gi < lim) ? __ldcg(src + gi) : NEG;
-      }
-    }
-  }
-  __syncthreads();
-  // 2. payoff table, padded per segment to a multiple of R with -inf
-  {
-    const float* price_t = p.price + as.off_price + (size_t)(t - 1) * K;
     const float* cost = p.cost + as.off_cost;
-    const int total = M * K * rs;
-    for (int i = tid; i < total; i += nth) {
-      const int j = i % rs;
-      const int mk = i / rs;
-      const int k = mk % K, m = mk / K;
+    for (int i = tid; i < M * rs; i += nth) {
+      const int m = i / rs, j = i - m * rs;
       Seg g0, g1;
       segments(as, m, g0, g1);
       const int L0p = round_up(g0.len, R);
-      float v = NEG;
       int a = -1;
       float sw = 0.f;
       if (j < L0p) {
-        if (j < g0.len) { a = g0.a0 + j; sw = g0.sw; }
+        if (j < g0.len) {
+          a = g0.a0 + j;
+          sw = g0.sw;
+        }
       } else if (j - L0p < g1.len) {
         a = g1.a0 + (j - L0p);
         sw = g1.sw;
       }
-      if (a >= 0)
-        v = (fmaf(__ldg(price_t + k), __ldg(as.e + a), -__ldg(cost + a)) - sw) + s_delta[k];
-      Rt[i] = v;
+      sm.Ecol[i] = a >= 0 ? __ldg(as.e + a) : 0.f;
+      sm.Ccol[i] = a >= 0 ? -__ldg(cost + a) - sw : NEG;
     }
   }
-  if (t > as.t_lo) load_trans(p, as, t - 1, Ps);
   __syncthreads();
+  if (tid < K) {
+    const double cr = sm.lvl[0] * rho_k;
+    sm.delta[tid] = (float)(cr - sm.lvl[1]);
+    sm.lam[tid] = lam_k;
+    if (w.tile == 0) as.evoff[(size_t)(t - 1) * K + tid] = cr;
+  }
+  __syncthreads();
+  for (int row = warp; row < M * K; row += nwarps) {
+    const int m = row / K, k = row - m * K;
+    const float lam = sm.lam[k], dl = sm.delta[k];
+    const float* ec = sm.Ecol + m * rs;
+    const float* cc = sm.Ccol + m * rs;
+    float* dst = sm.Rt + (size_t)row * rs;
+    for (int j = lane; j < rs; j += 32) dst[j] = fmaf(lam, ec[j], cc[j]) + dl;
+  }
+  cp_async_wait_all();
+  if (tma) {
+    if (tid == 0 && !mbar_wait_bounded(sm.bar, parity, p)) *(volatile int*)sm.abort = 1;
+    parity ^= 1u;
+  }
+  __syncthreads();
+  if (*(volatile int*)sm.abort) return false;
 
   // 3. banded max-plus with a register window of R rows
   const int MWK = M * W * K;
-  int* Xi = reinterpret_cast<int*>(Xs + (size_t)as.parts * MWK);
+  int* Xi = reinterpret_cast<int*>(sm.Xs + (size_t)as.parts * MWK);
   const int nact = K * as.nb * M * as.parts;
   if (tid < nact) {
     const int k = tid % K;
@@ -233,7 +384,7 @@ __device__ void stage(const SweepParams& p, const AssetDev& as, const WorkItem& 
     const int n0 = round_up(g0.len, R) / R;
     const int nc = n0 + round_up(g1.len, R) / R;
     const int c_lo = part * nc / as.parts, c_hi = (part + 1) * nc / as.parts;
-    const float* rt = Rt + (size_t)(m * K + k) * rs;
+    const float* rt = sm.Rt + (size_t)(m * K + k) * rs;
     float best[R];
     int bc[R];
 #pragma unroll
@@ -247,7 +398,7 @@ __device__ void stage(const SweepParams& p, const AssetDev& as, const WorkItem& 
       const int a0 = second ? g1.a0 : g0.a0;
       const int src = second ? g1.src : g0.src;
       const int toff = second ? n0 * R : 0;
-      const float* eb = Es + ((size_t)src * rows + b * R + a0 + u0) * K + k;
+      const float* eb = sm.Es + ((size_t)src * rows + b * R + a0 + u0) * K + k;
       float wv[2 * R - 1];
 #pragma unroll
       for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * K];
@@ -256,11 +407,12 @@ __device__ void stage(const SweepParams& p, const AssetDev& as, const WorkItem& 
       for (int i = 0; i < R; ++i) rr[i] = rt[toff + u0 + i];
       float cm[R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) cm[j] = rr[0] + wv[j];
+      for (int j = 0; j < R; ++j) cm[j] = fmaxf(rr[0] + wv[j], rr[1] + wv[j + 1]);
 #pragma unroll
-      for (int i = 1; i < R; ++i) {
+      for (int i = 2; i < R; i += 2) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) cm[j] = fmaxf(cm[j], rr[i] + wv[i + j]);
+        for (int j = 0; j < R; ++j)
+          cm[j] = max3f(cm[j], rr[i] + wv[i + j], rr[i + 1] + wv[i + 1 + j]);
       }
 #pragma unroll
       for (int j = 0; j < R; ++j) {
@@ -282,96 +434,117 @@ __device__ void stage(const SweepParams& p, const AssetDev& as, const WorkItem& 
         const int a0 = second ? g1.a0 : g0.a0;
         const int src = second ? g1.src : g0.src;
         const int toff = second ? n0 * R : 0;
-        const float* eb = Es + ((size_t)src * rows + b * R + j + a0 + u0) * K + k;
-        for (int i = 0; i < R; ++i) {
-          const float v = rt[toff + u0 + i] + eb[(size_t)i * K];
-          if (v == best[j]) {
-            arg = a0 + u0 + i;
-            break;
-          }
-        }
+        const float* eb = sm.Es + ((size_t)src * rows + b * R + j + a0 + u0) * K + k;
+        const float* rp = rt + toff + u0;
+        float v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = rp[i] + eb[(size_t)i * K];
+        int first = R - 1;
+#pragma unroll
+        for (int i = R - 1; i >= 0; --i)
+          if (v[i] == best[j]) first = i;
+        arg = a0 + u0 + first;
       }
-      Xs[xo + j * K] = best[j];
+      sm.Xs[xo + j * K] = best[j];
       Xi[xo + j * K] = arg;
     }
   }
   __syncthreads();
 
-  // 4. combine the action parts (in increasing action order), store V_t and
-  //    the policy
+  // 4. combine the action parts (in increasing action order); V'_t, policy
   {
     const size_t MNK = mnk(as);
-    const int total = M * W * K;
-    for (int i = tid; i < total; i += nth) {
-      const int k = i % K;
-      const int r = (i / K) % W;
-      const int m = i / (K * W);
+    const int Wt = w.s1 - w.s0, Kv = K + 1;
+    const double lvl = sm.lvl[1];
+    for (int row = warp; row < M * Wt; row += nwarps) {
+      const int m = row / Wt, r = row - m * Wt;
       const int s = w.s0 + r;
-      if (s >= w.s1) continue;
-      float bv = Xs[i];
-      int ba = Xi[i];
-      for (int q = 1; q < as.parts; ++q) {
-        const float v = Xs[q * MWK + i];
-        if (v > bv) {
-          bv = v;
-          ba = Xi[q * MWK + i];
+      for (int k = lane; k < K; k += 32) {
+        const int i = (m * W + r) * K + k;
+        float bv = sm.Xs[i];
+        int ba = Xi[i];
+        for (int qq = 1; qq < as.parts; ++qq) {
+          const float v = sm.Xs[qq * MWK + i];
+          if (v > bv) {
+            bv = v;
+            ba = Xi[qq * MWK + i];
+          }
         }
+        sm.Vs[(m * W + r) * Kv + k] = bv;
+        const size_t o = ((size_t)m * N + s) * K + k;
+        if (as.policy) {
+          const size_t po = (size_t)(t - as.policy_t_base) * MNK + o;
+          if (as.policy_bytes == 2)
+            __stcs(reinterpret_cast<short*>(as.policy) + po, (short)ba);
+          else
+            __stcs(reinterpret_cast<int*>(as.policy) + po, ba);
+        }
+        if (as.v_keep) __stcg(as.v_keep + (size_t)(t - as.t_lo) * MNK + o, bv);
+        if (as.ckpt && as.ckpt_every > 0 && t > 1 && (t - 1) % as.ckpt_every == 0)
+          __stcg(as.ckpt + (size_t)((t - 1) / as.ckpt_every - 1) * MNK + o, bv);
+        if (t == 1 && p.v1) p.v1[as.off_v1 + o] = (float)((double)bv + lvl);
       }
-      Vs[i] = bv;
-      const size_t o = ((size_t)m * N + s) * K + k;
-      if (as.policy) {
-        const size_t po = (size_t)(t - as.policy_t_base) * MNK + o;
-        if (as.policy_bytes == 2)
-          __stcs(reinterpret_cast<short*>(as.policy) + po, (short)ba);
-        else
-          __stcs(reinterpret_cast<int*>(as.policy) + po, ba);
-      }
-      if (as.v_keep) __stcg(as.v_keep + (size_t)(t - as.t_lo) * MNK + o, bv);
-      if (as.ckpt && as.ckpt_every > 0 && t > 1 && (t - 1) % as.ckpt_every == 0)
-        __stcg(as.ckpt + (size_t)((t - 1) / as.ckpt_every - 1) * MNK + o, bv);
-      if (t == 1 && p.v1) p.v1[as.off_v1 + o] = (float)((double)bv + s_lvl[1]);
     }
   }
   __syncthreads();
 
-  // 5. EV_{t-1} for the item's own rows
-  if (t > as.t_lo) expectation(as, w, t - 1, Ps, Vs, ev_ptr(as, t - 1));
+  // 5. EV'_{t-1} of the item's own rows
+  if (t > as.t_lo) expectation(as, w, t - 1, sm.Ps, sm.Vs, ev_ptr(as, t - 1));
+  return true;
 }
 
 template <int R>
 __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
-  float* Es = smem + p.sm_E;
-  float* Rt = smem + p.sm_R;
-  float* Vs = smem + p.sm_V;
-  float* Ps = smem + p.sm_P;
-  float* Xs = smem + p.sm_X;
   __shared__ int s_abort;
   __shared__ double s_lvl[2];
+  __shared__ float s_lam[128];
   __shared__ float s_delta[128];
+  __shared__ float s_ref;
+  __shared__ __align__(8) uint64_t s_bar;
+  Smem sm;
+  sm.Es = smem + p.sm_E;
+  sm.Rt = smem + p.sm_R;
+  sm.Vs = smem + p.sm_V;
+  sm.Ps = smem + p.sm_P;
+  sm.Xs = smem + p.sm_X;
+  sm.Ecol = smem + p.sm_C;
+  sm.Ccol = sm.Ecol;
+  sm.lvl = s_lvl;
+  sm.lam = s_lam;
+  sm.delta = s_delta;
+  sm.ref = &s_ref;
+  sm.abort = &s_abort;
+  sm.bar = &s_bar;
   const int i0 = p.cta_items[blockIdx.x], i1 = p.cta_items[blockIdx.x + 1];
-  if (threadIdx.x == 0) s_abort = 0;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    mbar_init(&s_bar);
+  }
   __syncthreads();
+  uint32_t parity = 0;
 
-  // prologue: EV_{t_hi} = P_{t_hi} V_{t_hi+1} for the item's rows
+  // prologue: EV'_{t_hi} = P_{t_hi} V'_{t_hi+1} for the item's rows
   for (int it = i0; it < i1; ++it) {
     const WorkItem w = p.items[it];
     const AssetDev& as = p.assets[w.asset];
     const float* vst = as.v_start ? as.v_start : p.terminal + as.off_terminal;
-    load_trans(p, as, as.t_hi, Ps);
+    prefetch_trans(p, as, as.t_hi, sm.Ps);
     const int Wt = w.s1 - w.s0, K = as.K;
     for (int i = threadIdx.x; i < as.M * Wt * K; i += blockDim.x) {
       const int k = i % K, r = (i / K) % Wt, m = i / (K * Wt);
-      Vs[(m * as.W + r) * K + k] = __ldcg(vst + ((size_t)m * as.N + w.s0 + r) * K + k);
+      sm.Vs[(m * as.W + r) * (K + 1) + k] =
+          __ldcg(vst + ((size_t)m * as.N + w.s0 + r) * K + k);
     }
     if (threadIdx.x == 0) {
       const double c0 = as.c_start ? *as.c_start : 0.0;
       p.item_c[it] = c0;
       if (w.tile == 0) as.off[as.t_hi + 1] = c0;
     }
+    cp_async_wait_all();
     __syncthreads();
-    expectation(as, w, as.t_hi, Ps, Vs, ev_ptr(as, as.t_hi));
+    expectation(as, w, as.t_hi, sm.Ps, sm.Vs, ev_ptr(as, as.t_hi));
     publish(p.flags + as.flag_base + w.tile, 1);
     __syncthreads();
   }
@@ -381,32 +554,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
       const WorkItem w = p.items[it];
       const AssetDev& as = p.assets[w.asset];
       if (g > as.t_hi - as.t_lo) continue;
-      if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, &s_abort)) return;
-      stage<R>(p, as, w, it, as.t_hi - g, Es, Rt, Vs, Ps, Xs, s_lvl, s_delta);
+      sm.Ccol = sm.Ecol + as.M * as.rs;
+      if (!item_stage<R>(p, as, w, it, g, sm, parity)) return;
       publish(p.flags + as.flag_base + w.tile, g + 2);
     }
   }
-}
-
-template <int R>
-cudaError_t launch_R(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
-  auto fn = sweep_kernel<R>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-  if (e != cudaSuccess) return e;
-  SweepParams pp = p;
-  void* args[] = {&pp};
-  return cudaLaunchCooperativeKernel((const void*)fn, dim3(s.grid), dim3(s.block), args, s.smem,
-                                     stream);
-}
-
-template <int R>
-int max_blocks_R(int block, size_t smem) {
-  auto fn = sweep_kernel<R>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 0;
-  return n;
 }
 
 // rho_t[k] = sum_k2 trans[t][k][k2] in double, for every asset of a launch
@@ -430,6 +582,27 @@ __global__ void ev_readout_kernel(const float* evp, const double* evoff, int M, 
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     out[i] = (float)((double)evp[i] + evoff[i % K]);
+}
+
+template <int R>
+cudaError_t launch_R(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
+  auto fn = sweep_kernel<R>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+  if (e != cudaSuccess) return e;
+  SweepParams pp = p;
+  void* args[] = {&pp};
+  return cudaLaunchCooperativeKernel((const void*)fn, dim3(s.grid), dim3(s.block), args, s.smem,
+                                     stream);
+}
+
+template <int R>
+int max_blocks_R(int block, size_t smem) {
+  auto fn = sweep_kernel<R>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 0;
+  return n;
 }
 
 }  // namespace
