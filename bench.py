@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--only", default="", help="run one sub-benchmark: config3|config4|config5")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", default="",
+                    help="config3-64 | config2: one solve inside the NVTX range 'esdp_profile' "
+                         "(for ncu --nvtx --nvtx-include esdp_profile/)")
     return ap.parse_args()
 
 
@@ -458,8 +461,50 @@ def bench_config5(torch, E, I, stream, flush, args, n_sm, f_max):
 EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5}
 
 
+def run_profile_case(name):
+    """One autotuned solve of a small case inside an NVTX range, nothing
+    else timed: the target of ncu captures."""
+    import torch
+    from paper_2511_15629_b300 import esdp as E
+    from paper_2511_15629_b300 import instances as I
+    if name == "config3-64":
+        full = I.config3()
+        n = 64
+        inst = I.Instance("config3_last64", n, full.N, full.K, full.A, full.D_dis, full.D_chg, 1,
+                          full.s_max, full.tau, full.eta_c, full.eta_d, 0.0,
+                          full.price[-n:].copy(), full.trans[-n:].copy(), full.cost,
+                          full.terminal, s0=full.s0)
+    elif name == "config2":
+        inst = I.config2()
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in E.concat_inputs([inst]).items()}
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    s = E.Solver([inst], device_ptrs=True, keep_ev=(name == "config2"))
+    s.autotune()
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("esdp_profile")
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    if name == "config2":
+        nh = inst.T * inst.n_modes * inst.K
+        n_bp = torch.empty(nh, dtype=torch.int32, device="cuda")
+        idx = torch.empty(nh * inst.N, dtype=torch.int32, device="cuda")
+        slope = torch.empty(nh * inst.N, device="cuda")
+        s.bid_curves(0, 1, inst.T + 1, n_bp, idx, slope)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    print(json.dumps({"profile_case": name, "launch": s.launch_info()}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        run_profile_case(args.profile_case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -78,6 +78,7 @@ struct esdp_ctx {
   std::vector<double*> d_off;     // per asset [T+2] level c_t
   std::vector<double*> d_evoff;   // per asset [T][K] EV_t - EV'_t
   std::vector<float*> d_refh;     // per asset [T+2] reference EV' entries
+  std::vector<float*> d_ptrans;   // per asset [T][K][Kp4] transposed transition matrices
   float* d_scratch = nullptr;     // readout staging (host mode), max MNK floats
   float* d_in_price = nullptr;    // host-mode input copies
   float* d_in_trans = nullptr;
@@ -184,7 +185,7 @@ int n_chunks_min(const esdp_asset& a, int R) {
 // Pick rows per tile and the action split for one asset given the share of
 // the grid (CTAs) it should occupy.
 bool choose_asset(const esdp_asset& a, int R, int block, double cta_share, AssetChoice* out) {
-  const int KM = a.K * a.n_modes;
+  const int KM = ((a.K + 1) / 2) * a.n_modes;  // max-plus threads per row block: price-state pairs
   const int nb_max = block / KM;
   if (nb_max < 1) return false;
   const double rows_per_cta = a.N / std::max(cta_share, 1e-9);
@@ -279,6 +280,7 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     d.off = c->d_off[ids[j]];
     d.evoff = c->d_evoff[ids[j]];
     d.c_start = nullptr;
+    d.ptrans = c->d_ptrans[ids[j]];
     plan->max_rows = std::max(plan->max_rows, a.T * a.K);
     plan->adev.push_back(d);
     for (int tI = 0; tI < d.n_tiles; ++tI) {
@@ -457,8 +459,8 @@ int plan_default(esdp_ctx* c, const std::vector<int>& ids, Plan* plan) {
   int best_rc = ESDP_EINVAL;
   double best_score = 1e300;
   Plan best;
-  for (int R : {8, 12, 16, 4}) {
-    for (int block : {256, 512, 128}) {
+  for (int R : {8, 10, 12, 6, 4}) {
+    for (int block : {256, 512, 384, 128}) {
       Plan p;
       std::string keep = c->err;
       int rc = build_plan(c, ids, R, block, c->n_sm, &p);
@@ -620,6 +622,9 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
     c->d_off.push_back(off);
     c->d_evoff.push_back(evoff);
     c->d_refh.push_back(refh);
+    float* pt = nullptr;
+    if ((rc = dalloc(c, &pt, (size_t)a.T * a.K * p_stride(a.K)))) return rc;
+    c->d_ptrans.push_back(pt);
   }
   {
     size_t mx = 0;
@@ -1018,7 +1023,7 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   CK(cudaEventCreate(&e1), "event");
   double best_ms = 1e300;
   int best_R = c->main.shape.R, best_block = c->main.shape.block;
-  for (int R : {4, 8, 12, 16}) {
+  for (int R : {4, 6, 8, 10, 12}) {
     for (int block : {128, 256, 384, 512}) {
       Plan p;
       std::string keep = c->err;

@@ -8,7 +8,7 @@ namespace esdp {
 
 // Rows of the SoC grid a thread owns in the banded max-plus (its register
 // window), one launch uses one value.
-constexpr int kRowsPerThreadChoices[] = {4, 8, 12, 16};
+constexpr int kRowsPerThreadChoices[] = {4, 6, 8, 10, 12};
 constexpr int kMaxBlock = 512;
 constexpr int kMaxWaits = 64;     // neighbour tiles a work item may wait on
 
@@ -47,6 +47,7 @@ struct AssetDev {
   double* off;          // [T+2]: off[t] = c_t (written by tile 0)
   double* evoff;        // [T][K]: EV_t - EV'_t = c_{t+1} rho_t[k] (written by tile 0)
   const double* c_start;  // c_{t_hi+1}, or nullptr for 0
+  float* ptrans;        // [T][K][p_stride(K)] transposed, padded P_t (prep kernel), or nullptr
 };
 
 struct WorkItem {
@@ -72,6 +73,13 @@ struct SweepParams {
   int sm_E, sm_R, sm_C, sm_V, sm_P, sm_X;
 };
 
+// Row strides of the V' tile and of the transposed transition matrix in
+// shared memory (and of the prepared transposed copy in global memory),
+// padded so that tensor-core fragment loads and float4 reads are free of bank
+// conflicts.
+__host__ __device__ inline int v_stride(int K) { return K + 4; }
+__host__ __device__ inline int p_stride(int K) { return ((K + 3) & ~3) + 8; }
+
 // Shared-memory carve-up of the sweep kernel (offsets in floats, every region
 // 128-byte aligned so that bulk copies and float4 accesses are aligned).
 struct SweepSmem {
@@ -80,14 +88,14 @@ struct SweepSmem {
 };
 inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R, int parts) {
   auto al = [](long long x) { return (int)((x + 31) / 32 * 32); };
-  const int rows = W + A + R, rs = (A + 2 * R) | 1, Kp4 = (K + 3) & ~3;
+  const int rows = W + A + R, rs = (A + 2 * R) | 1;
   SweepSmem s;
   s.E = 0;
-  s.Rt = s.E + al((long long)M * rows * K);
-  s.C = s.Rt + al((long long)M * K * rs);
+  s.Rt = s.E + al((long long)M * rows * (K + (K & 1)));
+  s.C = s.Rt;  // no payoff table: the payoffs are formed in registers
   s.V = s.C + al(2LL * M * rs);
-  s.P = s.V + al((long long)M * W * (K + 1));
-  s.X = s.P + al((long long)K * Kp4);
+  s.P = s.V + al((long long)M * W * v_stride(K));
+  s.X = s.P + al((long long)K * p_stride(K));
   s.bytes = (size_t)(s.X + al(2LL * parts * M * W * K)) * sizeof(float);
   return s;
 }
@@ -102,7 +110,9 @@ struct SweepShape {
 
 cudaError_t launch_sweep(const SweepShape& shape, const SweepParams& p, cudaStream_t stream);
 int sweep_max_blocks_per_sm(int R, int block, size_t smem);
-// Row sums (double) of every transition matrix of the launch's assets.
+// Instance preparation for a launch: row sums (double) of every transition
+// matrix and, where the asset has a buffer for it, the transposed padded copy
+// ptrans[t][k2][k] = trans[t][k][k2].
 cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows, const float* trans,
                            cudaStream_t stream);
 // out[m][s][k] = EV'_t + evoff_t[k] rounded to float (the reported EV_t).

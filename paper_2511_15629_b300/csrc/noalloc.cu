@@ -106,9 +106,9 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
     return msg(err, err_len, ESDP_ECUDA, "device attribute query failed");
 
   // launch shape: R = 8 rows per thread, 512 threads, tiles sized to the grid
-  const int R = 8, block = 512, M = a.n_modes, K = a.K, KM = K * M;
+  const int R = 8, block = 512, M = a.n_modes, K = a.K, KM = ((K + 1) / 2) * M;
   const int nb_max = block / KM;
-  if (nb_max < 1) return msg(err, err_len, ESDP_EINVAL, "K * n_modes exceeds 512");
+  if (nb_max < 1) return msg(err, err_len, ESDP_EINVAL, "K * n_modes exceeds 1024");
   int nb = std::max(1, std::min(nb_max, (a.N + n_sm * R - 1) / (n_sm * R)));
   int W = 0, tiles = 0, parts = 1, rows = 0, rs = 0;
   SweepSmem L{};

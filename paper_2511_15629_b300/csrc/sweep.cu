@@ -59,6 +59,23 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
   return r;
 }
 
+// Two independent round-to-nearest float32 operations per instruction
+// (one per price state of a pair); each lane equals the scalar operation.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long x = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long y = *reinterpret_cast<unsigned long long*>(&b), r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return *reinterpret_cast<float2*>(&r);
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long x = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long y = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long z = *reinterpret_cast<unsigned long long*>(&c), r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(y), "l"(z));
+  return *reinterpret_cast<float2*>(&r);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -154,64 +171,198 @@ __device__ __forceinline__ float* ev_ptr(const AssetDev& as, int t) {
 // Issue the asynchronous load of P_t transposed: Ps[k2*Kp4 + k] = trans[t][k][k2].
 __device__ __forceinline__ void prefetch_trans(const SweepParams& p, const AssetDev& as, int t,
                                                float* Ps) {
-  const int K = as.K, Kp4 = (K + 3) & ~3;
+  const int K = as.K, Kpt = p_stride(K);
   const float* P = p.trans + as.off_trans + (size_t)(t - 1) * K * K;
   for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
     const int k2 = i / K, k = i - k2 * K;
-    cp_async4(Ps + k2 * Kp4 + k, P + (size_t)k * K + k2);
+    cp_async4(Ps + k2 * Kpt + k, P + (size_t)k * K + k2);
   }
+}
+
+// Start loading P_t^T into shared memory: one bulk copy of the prepared
+// transposed copy when there is one (completion on `bar`), else the cp.async
+// gather above.  Returns true if a bulk copy was issued.
+__device__ __forceinline__ bool load_trans_async(const SweepParams& p, const AssetDev& as, int t,
+                                                 float* Ps, uint64_t* bar) {
+  if (as.ptrans) {
+    if (threadIdx.x == 0) {
+      const int K = as.K, Kpt = p_stride(K);
+      const uint32_t bytes = (uint32_t)K * Kpt * 4u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, bytes);
+      bulk_load(Ps, as.ptrans + (size_t)(t - 1) * K * Kpt, bytes, bar);
+    }
+    return true;
+  }
+  prefetch_trans(p, as, t, Ps);
+  return false;
 }
 
 // EV rows of the item (eq. 6) from V' in shared memory (row stride K+1):
-// each thread forms 2 rows x 4 price states; the sum over k2 runs in
-// ascending order with one fma per term.  `te` is the stage of the EV being
-// produced; its reference entry also goes to its own per-stage slot.
-__device__ __forceinline__ void expectation(const AssetDev& as, const WorkItem& w, int te,
-                                            const float* Ps, const float* Vs, float* dst) {
-  const int K = as.K, M = as.M, W = as.W, N = as.N, Kv = K + 1, Kp4 = (K + 3) & ~3;
+// each thread forms NR rows x 4 price states from float4 reads of P^T; the
+// sum over k2 runs in ascending order with one fma per term.  `te` is the
+// stage of the EV being produced; its reference entry also goes to its own
+// per-stage slot.
+template <int NR>
+__device__ __forceinline__ void expectation_rows(const AssetDev& as, const WorkItem& w, int te,
+                                                 const float* Ps, const float* Vs, float* dst) {
+  const int K = as.K, M = as.M, W = as.W, N = as.N, Kv = v_stride(K), Kpt = p_stride(K);
   const int Wt = w.s1 - w.s0;
   const int G = (K + 3) >> 2;
   const int n_rows = M * Wt;
-  const int units = ((n_rows + 1) >> 1) * G;
+  const int units = ((n_rows + NR - 1) / NR) * G;
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
     const int g = u % G, rp = u / G;
-    const int L0 = 2 * rp, L1 = min(2 * rp + 1, n_rows - 1);
-    const int m0 = L0 / Wt, r0 = L0 - m0 * Wt;
-    const int m1 = L1 / Wt, r1 = L1 - m1 * Wt;
-    const float* v0 = Vs + (m0 * W + r0) * Kv;
-    const float* v1 = Vs + (m1 * W + r1) * Kv;
-    const float* pp = Ps + 4 * g;
-    float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k2 = 0; k2 < K; ++k2) {
-      const float4 q = *reinterpret_cast<const float4*>(pp + k2 * Kp4);
-      const float x0 = v0[k2], x1 = v1[k2];
-      a0[0] = fmaf(q.x, x0, a0[0]);
-      a0[1] = fmaf(q.y, x0, a0[1]);
-      a0[2] = fmaf(q.z, x0, a0[2]);
-      a0[3] = fmaf(q.w, x0, a0[3]);
-      a1[0] = fmaf(q.x, x1, a1[0]);
-      a1[1] = fmaf(q.y, x1, a1[1]);
-      a1[2] = fmaf(q.z, x1, a1[2]);
-      a1[3] = fmaf(q.w, x1, a1[3]);
-    }
-    float* d0 = dst + ((size_t)m0 * N + w.s0 + r0) * K + 4 * g;
+    const float* v[NR];
+    int mm[NR], rr[NR];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (4 * g + j < K) __stcg(d0 + j, a0[j]);
-    if (m0 == 0 && g == 0 && w.s0 + r0 == as.ref_row) __stcg(as.ref_hist + te, a0[0]);
-    if (2 * rp + 1 < n_rows) {
-      float* d1 = dst + ((size_t)m1 * N + w.s0 + r1) * K + 4 * g;
+    for (int q = 0; q < NR; ++q) {
+      const int L = min(NR * rp + q, n_rows - 1);
+      mm[q] = L / Wt;
+      rr[q] = L - mm[q] * Wt;
+      v[q] = Vs + (mm[q] * W + rr[q]) * Kv;
+    }
+    const float* pp = Ps + 4 * g;
+    float a[NR][4];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) a[q][0] = a[q][1] = a[q][2] = a[q][3] = 0.f;
+#pragma unroll 4
+    for (int k2 = 0; k2 < K; ++k2) {
+      const float4 pq = *reinterpret_cast<const float4*>(pp + k2 * Kpt);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const float x = v[q][k2];
+        a[q][0] = fmaf(pq.x, x, a[q][0]);
+        a[q][1] = fmaf(pq.y, x, a[q][1]);
+        a[q][2] = fmaf(pq.z, x, a[q][2]);
+        a[q][3] = fmaf(pq.w, x, a[q][3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      if (NR * rp + q >= n_rows) break;
+      float* d = dst + ((size_t)mm[q] * N + w.s0 + rr[q]) * K + 4 * g;
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (4 * g + j < K) __stcg(d1 + j, a1[j]);
-      if (m1 == 0 && g == 0 && w.s0 + r1 == as.ref_row) __stcg(as.ref_hist + te, a1[0]);
+        if (4 * g + j < K) __stcg(d + j, a[q][j]);
+      if (mm[q] == 0 && g == 0 && w.s0 + rr[q] == as.ref_row) __stcg(as.ref_hist + te, a[q][0]);
     }
   }
 }
 
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = hi + lo with hi, lo exactly representable in tf32 (lo carries the next
+// 11 bits): the products hi*hi + hi*lo + lo*hi keep float32 accuracy.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// EV rows of the item on the tensor cores (K a multiple of 8): the dense
+// product [M*Wt x K] = V' [M*Wt x K] . P^T [K x K] in 16x8x8 tf32 tiles,
+// float32-accurate through the three-product split, float32 accumulation.
+// A warp owns one 16-row block and two 8-column blocks at a time.
+__device__ void expectation_mma(const AssetDev& as, const WorkItem& w, int te, const float* Ps,
+                                const float* Vs, float* dst) {
+  const int K = as.K, M = as.M, W = as.W, N = as.N, Kv = v_stride(K), Kpt = p_stride(K);
+  const int Wt = w.s1 - w.s0, n_rows = M * Wt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int MT = (n_rows + 15) >> 4, NT2 = ((K >> 3) + 1) >> 1;
+  for (int u = warp; u < MT * NT2; u += nwarps) {
+    const int mt = u / NT2, nt = (u - mt * NT2) * 2;
+    const bool two = nt + 1 < (K >> 3);
+    // the two A rows of this lane (clamped: rows past the tile are computed, not stored)
+    const int L0 = min(mt * 16 + gq, n_rows - 1), L1 = min(mt * 16 + gq + 8, n_rows - 1);
+    const int m0 = L0 / Wt, r0 = L0 - m0 * Wt, m1 = L1 / Wt, r1 = L1 - m1 * Wt;
+    const float* A0 = Vs + (m0 * W + r0) * Kv;
+    const float* A1 = Vs + (m1 * W + r1) * Kv;
+    // independent accumulators (by product term and by k-step parity) keep
+    // the chains of dependent mma short; they are summed at the end
+    float hh[2][2][4] = {}, xx[2][2][4] = {};  // [n-tile][k parity][frag]
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      const int par = (k0 >> 3) & 1;
+      uint32_t ah[4], al[4];
+      split_tf32(A0[k0 + tq], ah[0], al[0]);
+      split_tf32(A1[k0 + tq], ah[1], al[1]);
+      split_tf32(A0[k0 + tq + 4], ah[2], al[2]);
+      split_tf32(A1[k0 + tq + 4], ah[3], al[3]);
+      const float* B = Ps + (k0 + tq) * Kpt + nt * 8 + gq;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(B[8 * h], bh0, bl0);
+        split_tf32(B[4 * Kpt + 8 * h], bh1, bl1);
+        if (par == 0) {
+          mma_tf32(xx[h][0], al, bh0, bh1);
+          mma_tf32(xx[h][0], ah, bl0, bl1);
+          mma_tf32(hh[h][0], ah, bh0, bh1);
+        } else {
+          mma_tf32(xx[h][1], al, bh0, bh1);
+          mma_tf32(xx[h][1], ah, bl0, bl1);
+          mma_tf32(hh[h][1], ah, bh0, bh1);
+        }
+      }
+    }
+    float d0[4], d1[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      d0[f] = (hh[0][0][f] + hh[0][1][f]) + (xx[0][0][f] + xx[0][1][f]);
+      d1[f] = (hh[1][0][f] + hh[1][1][f]) + (xx[1][0][f] + xx[1][1][f]);
+    }
+    // d[0..1]: row gq, columns 2tq, 2tq+1; d[2..3]: row gq + 8
+#pragma unroll
+    for (int hrow = 0; hrow < 2; ++hrow) {
+      const int L = mt * 16 + gq + 8 * hrow;
+      if (L >= n_rows) continue;
+      const int m = L / Wt, r = L - m * Wt;
+      float* drow = dst + ((size_t)m * N + w.s0 + r) * K;
+      const int c0 = nt * 8 + 2 * tq;
+      __stcg(drow + c0, d0[2 * hrow]);
+      __stcg(drow + c0 + 1, d0[2 * hrow + 1]);
+      if (two) {
+        __stcg(drow + c0 + 8, d1[2 * hrow]);
+        __stcg(drow + c0 + 9, d1[2 * hrow + 1]);
+      }
+      if (m == 0 && c0 == 0 && w.s0 + r == as.ref_row) __stcg(as.ref_hist + te, d0[2 * hrow]);
+    }
+  }
+}
+
+__device__ __forceinline__ void expectation(const AssetDev& as, const WorkItem& w, int te,
+                                            const float* Ps, const float* Vs, float* dst) {
+  if ((as.K & 7) == 0) {
+    expectation_mma(as, w, te, Ps, Vs, dst);
+    return;
+  }
+  const int n_rows = as.M * (w.s1 - w.s0), G = (as.K + 3) >> 2;
+  if (((n_rows + 1) / 2) * G * 4 >= (int)blockDim.x * 3)
+    expectation_rows<2>(as, w, te, Ps, Vs, dst);
+  else
+    expectation_rows<1>(as, w, te, Ps, Vs, dst);
+}
+
+// Release the item's EV rows: they are read by bulk copies (async proxy) of
+// other CTAs, hence the proxy fence before the release store.
 __device__ __forceinline__ void publish(int* flag, int v) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     __threadfence();
     st_release(flag, v);
   }
@@ -251,28 +402,31 @@ __device__ bool wait_neighbours(const SweepParams& p, const AssetDev& as, const 
 }
 
 struct Smem {
-  float *Es, *Rt, *Ecol, *Ccol, *Vs, *Ps, *Xs;
+  float *Es, *Vs, *Ps, *Xs;
+  float2* EC;      // [M][rs] (grid energy e_a, -(cost_a + switch)), -inf padding
   double* lvl;     // [2]: c_{t+1}, c_t
   float* lam;      // [K] prices of the stage
   float* delta;    // [K] level correction of the stage
   float* ref;      // EV'_t[ref]
   int* abort;
-  uint64_t* bar;
+  uint64_t* bar;   // EV tile bulk copies
+  uint64_t* barP;  // transposed P bulk copy
 };
 
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
-                           int g, const Smem& sm, uint32_t& parity) {
+                           int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
             nwarps = nth >> 5;
   const float NEG = -CUDART_INF_F;
   const bool tma = (K & 3) == 0;
+  const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
 
   // 0. prefetch the inputs of the stage
-  if (t > as.t_lo) prefetch_trans(p, as, t - 1, sm.Ps);
+  const bool p_bulk = t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP);
   float lam_k = 0.f;
   double rho_k = 0.0, c_next = 0.0;
   if (tid < K) {
@@ -281,47 +435,8 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   }
   if (tid == 0) c_next = p.item_c[it];
 
-  // 1. neighbours
-  if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
-
-  // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
-  const float* ev_t = ev_ptr(as, t);
-  const int g0row = w.s0 - as.D_dis;
-  const int lo = max(g0row, 0), hi = min(g0row + rows, N);
-  if (tma) {
-    if (tid == 0) {
-      asm volatile("fence.proxy.async;" ::: "memory");
-      const uint32_t bytes = (uint32_t)(hi - lo) * K * 4u;
-      mbar_expect_tx(sm.bar, bytes * M);
-      for (int m = 0; m < M; ++m)
-        bulk_load(sm.Es + ((size_t)m * rows + (lo - g0row)) * K, ev_t + ((size_t)m * N + lo) * K,
-                  bytes, sm.bar);
-    }
-  } else {
-    for (int m = 0; m < M; ++m) {
-      const float* src = ev_t + ((size_t)m * N + lo) * K;
-      float* dst = sm.Es + ((size_t)m * rows + (lo - g0row)) * K;
-      const int n = (hi - lo) * K;
-      for (int i = tid; i < n; i += nth) dst[i] = __ldcg(src + i);
-    }
-  }
-  {
-    const int below = (lo - g0row) * K, above0 = (hi - g0row) * K, total = rows * K;
-    for (int m = 0; m < M; ++m) {
-      float* e = sm.Es + (size_t)m * rows * K;
-      for (int i = tid; i < below; i += nth) e[i] = NEG;
-      for (int i = above0 + tid; i < total; i += nth) e[i] = NEG;
-    }
-  }
-  // level of the stage and the per-state correction of the payoffs
-  if (tid == 0) {
-    const double c_t = c_next + (double)*sm.ref;
-    sm.lvl[0] = c_next;
-    sm.lvl[1] = c_t;
-    p.item_c[it] = c_t;
-    if (w.tile == 0) as.off[t] = c_t;
-  }
-  // payoff columns of each mode: e_a and -(cost_a + switch), -inf padding
+  // payoff columns of each mode: (e_a, -(cost_a + switch)), -inf padding;
+  // the payoff r = price*e_a - cost_a is formed in the max-plus itself
   {
     const float* cost = p.cost + as.off_cost;
     for (int i = tid; i < M * rs; i += nth) {
@@ -340,9 +455,56 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
         a = g1.a0 + (j - L0p);
         sw = g1.sw;
       }
-      sm.Ecol[i] = a >= 0 ? __ldg(as.e + a) : 0.f;
-      sm.Ccol[i] = a >= 0 ? -__ldg(cost + a) - sw : NEG;
+      sm.EC[i] = a >= 0 ? make_float2(__ldg(as.e + a), -__ldg(cost + a) - sw) : make_float2(0.f, NEG);
     }
+  }
+  // 1. neighbours
+  if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
+
+  // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
+  const float* ev_t = ev_ptr(as, t);
+  const int g0row = w.s0 - as.D_dis;
+  const int lo = max(g0row, 0), hi = min(g0row + rows, N);
+  if (tma) {
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const uint32_t bytes = (uint32_t)(hi - lo) * K * 4u;
+      mbar_expect_tx(sm.bar, bytes * M);
+      for (int m = 0; m < M; ++m)
+        bulk_load(sm.Es + ((size_t)m * rows + (lo - g0row)) * K, ev_t + ((size_t)m * N + lo) * K,
+                  bytes, sm.bar);
+    }
+  } else {
+    for (int m = 0; m < M; ++m) {
+      const float* src = ev_t + ((size_t)m * N + lo) * K;
+      float* dst = sm.Es + ((size_t)m * rows + (lo - g0row)) * Ke;
+      const int n = (hi - lo) * K;
+      if (Ke == K) {
+        for (int i = tid; i < n; i += nth) dst[i] = __ldcg(src + i);
+      } else {
+        for (int i = tid; i < n; i += nth) {
+          const int r = i / K;
+          dst[i + r] = __ldcg(src + i);
+        }
+        for (int r = tid; r < hi - lo; r += nth) dst[r * Ke + K] = NEG;  // pad column
+      }
+    }
+  }
+  {
+    const int below = (lo - g0row) * Ke, above0 = (hi - g0row) * Ke, total = rows * Ke;
+    for (int m = 0; m < M; ++m) {
+      float* e = sm.Es + (size_t)m * rows * Ke;
+      for (int i = tid; i < below; i += nth) e[i] = NEG;
+      for (int i = above0 + tid; i < total; i += nth) e[i] = NEG;
+    }
+  }
+  // level of the stage and the per-state correction of the payoffs
+  if (tid == 0) {
+    const double c_t = c_next + (double)*sm.ref;
+    sm.lvl[0] = c_next;
+    sm.lvl[1] = c_t;
+    p.item_c[it] = c_t;
+    if (w.tile == 0) as.off[t] = c_t;
   }
   __syncthreads();
   if (tid < K) {
@@ -351,46 +513,48 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     sm.lam[tid] = lam_k;
     if (w.tile == 0) as.evoff[(size_t)(t - 1) * K + tid] = cr;
   }
-  __syncthreads();
-  for (int row = warp; row < M * K; row += nwarps) {
-    const int m = row / K, k = row - m * K;
-    const float lam = sm.lam[k], dl = sm.delta[k];
-    const float* ec = sm.Ecol + m * rs;
-    const float* cc = sm.Ccol + m * rs;
-    float* dst = sm.Rt + (size_t)row * rs;
-    for (int j = lane; j < rs; j += 32) dst[j] = fmaf(lam, ec[j], cc[j]) + dl;
-  }
+  if (tid == K && (K & 1)) sm.lam[K] = 0.f;  // pad state of an odd K
   cp_async_wait_all();
   if (tma) {
     if (tid == 0 && !mbar_wait_bounded(sm.bar, parity, p)) *(volatile int*)sm.abort = 1;
     parity ^= 1u;
   }
+  if (p_bulk) {
+    if (tid == 0 && !mbar_wait_bounded(sm.barP, parity_p, p)) *(volatile int*)sm.abort = 1;
+    parity_p ^= 1u;
+  }
   __syncthreads();
   if (*(volatile int*)sm.abort) return false;
 
-  // 3. banded max-plus with a register window of R rows
+  // 3. banded max-plus: a thread owns R consecutive rows of one mode and a
+  //    pair of price states; it slides a register window of EV pairs over the
+  //    action band, two evaluations per packed add and per 3-input max
   const int MWK = M * W * K;
   int* Xi = reinterpret_cast<int*>(sm.Xs + (size_t)as.parts * MWK);
-  const int nact = K * as.nb * M * as.parts;
+  const int Kh = Ke >> 1;
+  const int nact = Kh * as.nb * M * as.parts;
   if (tid < nact) {
-    const int k = tid % K;
-    int q = tid / K;
+    const int kp = tid % Kh;
+    int q = tid / Kh;
     const int b = q % as.nb;
     q /= as.nb;
     const int m = q % M;
     const int part = q / M;
+    const int k0 = 2 * kp;
     Seg g0, g1;
     segments(as, m, g0, g1);
     const int n0 = round_up(g0.len, R) / R;
     const int nc = n0 + round_up(g1.len, R) / R;
     const int c_lo = part * nc / as.parts, c_hi = (part + 1) * nc / as.parts;
-    const float* rt = sm.Rt + (size_t)(m * K + k) * rs;
-    float best[R];
-    int bc[R];
+    const float2* ec = sm.EC + m * rs;
+    const float2 lam = make_float2(sm.lam[k0], sm.lam[k0 + 1]);
+    float2 best[R];
+    int bx[R], by[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      best[j] = NEG;
-      bc[j] = -1;
+      best[j] = make_float2(NEG, NEG);
+      bx[j] = -1;
+      by[j] = -1;
     }
     for (int c = c_lo; c < c_hi; ++c) {
       const bool second = c >= n0;
@@ -398,67 +562,89 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
       const int a0 = second ? g1.a0 : g0.a0;
       const int src = second ? g1.src : g0.src;
       const int toff = second ? n0 * R : 0;
-      const float* eb = sm.Es + ((size_t)src * rows + b * R + a0 + u0) * K + k;
-      float wv[2 * R - 1];
+      const float2* eb =
+          reinterpret_cast<const float2*>(sm.Es + ((size_t)src * rows + b * R + a0 + u0) * Ke) + kp;
+      float2 wv[2 * R - 1];
 #pragma unroll
-      for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * K];
-      float rr[R];
+      for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
+      float2 rr[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) rr[i] = rt[toff + u0 + i];
-      float cm[R];
+      for (int i = 0; i < R; ++i) {
+        const float2 e = ec[toff + u0 + i];
+        rr[i] = fma2(lam, make_float2(e.x, e.x), make_float2(e.y, e.y));
+      }
+      float2 cm[R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) cm[j] = fmaxf(rr[0] + wv[j], rr[1] + wv[j + 1]);
+      for (int j = 0; j < R; ++j) {
+        const float2 x = add2(rr[0], wv[j]), y = add2(rr[1], wv[j + 1]);
+        cm[j] = make_float2(fmaxf(x.x, y.x), fmaxf(x.y, y.y));
+      }
 #pragma unroll
       for (int i = 2; i < R; i += 2) {
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-          cm[j] = max3f(cm[j], rr[i] + wv[i + j], rr[i + 1] + wv[i + 1 + j]);
+        for (int j = 0; j < R; ++j) {
+          const float2 x = add2(rr[i], wv[i + j]), y = add2(rr[i + 1], wv[i + 1 + j]);
+          cm[j] = make_float2(max3f(cm[j].x, x.x, y.x), max3f(cm[j].y, x.y, y.y));
+        }
       }
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        if (cm[j] > best[j]) {
-          best[j] = cm[j];
-          bc[j] = c;
+        if (cm[j].x > best[j].x) {
+          best[j].x = cm[j].x;
+          bx[j] = c;
+        }
+        if (cm[j].y > best[j].y) {
+          best[j].y = cm[j].y;
+          by[j] = c;
         }
       }
     }
     // exact argmax: first action of the winning chunk that reproduces the max
-    const int xo = part * MWK + (m * W + b * R) * K + k;
+    // (the same two round-to-nearest operations as the packed evaluation)
+    const int xo = part * MWK + (m * W + b * R) * K + k0;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      int arg = -1;
-      if (bc[j] >= 0) {
-        const int c = bc[j];
-        const bool second = c >= n0;
-        const int u0 = (second ? c - n0 : c) * R;
-        const int a0 = second ? g1.a0 : g0.a0;
-        const int src = second ? g1.src : g0.src;
-        const int toff = second ? n0 * R : 0;
-        const float* eb = sm.Es + ((size_t)src * rows + b * R + j + a0 + u0) * K + k;
-        const float* rp = rt + toff + u0;
-        float v[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = rp[i] + eb[(size_t)i * K];
-        int first = R - 1;
+      for (int h = 0; h < 2; ++h) {
+        const int c = h ? by[j] : bx[j];
+        const float bj = h ? best[j].y : best[j].x;
+        const float lk = h ? lam.y : lam.x;
+        int arg = -1;
+        if (c >= 0) {
+          const bool second = c >= n0;
+          const int u0 = (second ? c - n0 : c) * R;
+          const int a0 = second ? g1.a0 : g0.a0;
+          const int src = second ? g1.src : g0.src;
+          const int toff = second ? n0 * R : 0;
+          const float* eb = sm.Es + ((size_t)src * rows + b * R + j + a0 + u0) * Ke + k0 + h;
+          const float2* ep = ec + toff + u0;
+          float v[R];
 #pragma unroll
-        for (int i = R - 1; i >= 0; --i)
-          if (v[i] == best[j]) first = i;
-        arg = a0 + u0 + first;
+          for (int i = 0; i < R; ++i) {
+            const float2 e = ep[i];
+            v[i] = fmaf(lk, e.x, e.y) + eb[(size_t)i * Ke];
+          }
+          int first = R - 1;
+#pragma unroll
+          for (int i = R - 1; i >= 0; --i)
+            if (v[i] == bj) first = i;
+          arg = a0 + u0 + first;
+        }
+        if (k0 + h < K) {
+          sm.Xs[xo + j * K + h] = bj;
+          Xi[xo + j * K + h] = arg;
+        }
       }
-      sm.Xs[xo + j * K] = best[j];
-      Xi[xo + j * K] = arg;
     }
   }
   __syncthreads();
 
-  // 4. combine the action parts (in increasing action order); V'_t, policy
+  // 4. combine the action parts (in increasing action order) into part 0;
+  //    V'_t into the V tile
   {
-    const size_t MNK = mnk(as);
-    const int Wt = w.s1 - w.s0, Kv = K + 1;
-    const double lvl = sm.lvl[1];
+    const int Wt = w.s1 - w.s0, Kv = v_stride(K);
     for (int row = warp; row < M * Wt; row += nwarps) {
       const int m = row / Wt, r = row - m * Wt;
-      const int s = w.s0 + r;
       for (int k = lane; k < K; k += 32) {
         const int i = (m * W + r) * K + k;
         float bv = sm.Xs[i];
@@ -470,19 +656,10 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
             ba = Xi[qq * MWK + i];
           }
         }
+        bv += sm.delta[k];  // V'_t = max_a(r + EV') + c_{t+1} rho_t[k] - c_t
         sm.Vs[(m * W + r) * Kv + k] = bv;
-        const size_t o = ((size_t)m * N + s) * K + k;
-        if (as.policy) {
-          const size_t po = (size_t)(t - as.policy_t_base) * MNK + o;
-          if (as.policy_bytes == 2)
-            __stcs(reinterpret_cast<short*>(as.policy) + po, (short)ba);
-          else
-            __stcs(reinterpret_cast<int*>(as.policy) + po, ba);
-        }
-        if (as.v_keep) __stcg(as.v_keep + (size_t)(t - as.t_lo) * MNK + o, bv);
-        if (as.ckpt && as.ckpt_every > 0 && t > 1 && (t - 1) % as.ckpt_every == 0)
-          __stcg(as.ckpt + (size_t)((t - 1) / as.ckpt_every - 1) * MNK + o, bv);
-        if (t == 1 && p.v1) p.v1[as.off_v1 + o] = (float)((double)bv + lvl);
+        sm.Xs[i] = bv;
+        Xi[i] = ba;
       }
     }
   }
@@ -491,6 +668,40 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   // 5. EV'_{t-1} of the item's own rows
   if (t > as.t_lo) expectation(as, w, t - 1, sm.Ps, sm.Vs, ev_ptr(as, t - 1));
   return true;
+}
+
+// After the publish: the streaming outputs of the stage (policy, values kept
+// for the adjoint, checkpoints, V_1), read from the combined part-0 results.
+__device__ void item_outputs(const SweepParams& p, const AssetDev& as, const WorkItem& w, int t,
+                             const Smem& sm) {
+  const int K = as.K, M = as.M, N = as.N, W = as.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int MWK = M * W * K;
+  const int* Xi = reinterpret_cast<const int*>(sm.Xs + (size_t)as.parts * MWK);
+  const size_t MNK = mnk(as);
+  const int Wt = w.s1 - w.s0;
+  const double lvl = sm.lvl[1];
+  const bool ck = as.ckpt && as.ckpt_every > 0 && t > 1 && (t - 1) % as.ckpt_every == 0;
+  short* pol16 = as.policy_bytes == 2 ? reinterpret_cast<short*>(as.policy) : nullptr;
+  int* pol32 = as.policy_bytes == 4 ? reinterpret_cast<int*>(as.policy) : nullptr;
+  const size_t pbase = (size_t)(t - as.policy_t_base) * MNK;
+  float* vk = as.v_keep ? as.v_keep + (size_t)(t - as.t_lo) * MNK : nullptr;
+  float* cp = ck ? as.ckpt + (size_t)((t - 1) / as.ckpt_every - 1) * MNK : nullptr;
+  float* v1 = (t == 1 && p.v1) ? p.v1 + as.off_v1 : nullptr;
+  for (int row = warp; row < M * Wt; row += nwarps) {
+    const int m = row / Wt, r = row - m * Wt;
+    const size_t ob = ((size_t)m * N + w.s0 + r) * K;
+    const int ib = (m * W + r) * K;
+    for (int k = lane; k < K; k += 32) {
+      const float bv = sm.Xs[ib + k];
+      const int ba = Xi[ib + k];
+      if (pol32) __stcs(pol32 + pbase + ob + k, ba);
+      if (pol16) __stcs(pol16 + pbase + ob + k, (short)ba);
+      if (vk) __stcg(vk + ob + k, bv);
+      if (cp) __stcg(cp + ob + k, bv);
+      if (v1) v1[ob + k] = (float)((double)bv + lvl);
+    }
+  }
 }
 
 template <int R>
@@ -503,38 +714,55 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   __shared__ float s_delta[128];
   __shared__ float s_ref;
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_barP;
+  __shared__ __align__(16) AssetDev s_as;
   Smem sm;
   sm.Es = smem + p.sm_E;
-  sm.Rt = smem + p.sm_R;
+  sm.EC = reinterpret_cast<float2*>(smem + p.sm_C);
   sm.Vs = smem + p.sm_V;
   sm.Ps = smem + p.sm_P;
   sm.Xs = smem + p.sm_X;
-  sm.Ecol = smem + p.sm_C;
-  sm.Ccol = sm.Ecol;
   sm.lvl = s_lvl;
   sm.lam = s_lam;
   sm.delta = s_delta;
   sm.ref = &s_ref;
   sm.abort = &s_abort;
   sm.bar = &s_bar;
+  sm.barP = &s_barP;
   const int i0 = p.cta_items[blockIdx.x], i1 = p.cta_items[blockIdx.x + 1];
   if (threadIdx.x == 0) {
     s_abort = 0;
     mbar_init(&s_bar);
+    mbar_init(&s_barP);
   }
   __syncthreads();
-  uint32_t parity = 0;
+  uint32_t parity = 0, parity_p = 0;
+  // the work item's asset descriptor lives in shared memory: the loops that
+  // store to global memory then need not reload its fields
+  auto load_asset = [&](int a) {
+    const int n = (int)(sizeof(AssetDev) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(p.assets + a);
+    int* dst = reinterpret_cast<int*>(&s_as);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  };
+  int cur_asset = -1;
 
   // prologue: EV'_{t_hi} = P_{t_hi} V'_{t_hi+1} for the item's rows
   for (int it = i0; it < i1; ++it) {
     const WorkItem w = p.items[it];
-    const AssetDev& as = p.assets[w.asset];
+    if (w.asset != cur_asset) {
+      load_asset(w.asset);
+      cur_asset = w.asset;
+    }
+    const AssetDev& as = s_as;
     const float* vst = as.v_start ? as.v_start : p.terminal + as.off_terminal;
-    prefetch_trans(p, as, as.t_hi, sm.Ps);
+    const bool pb = load_trans_async(p, as, as.t_hi, sm.Ps, sm.barP);
     const int Wt = w.s1 - w.s0, K = as.K;
     for (int i = threadIdx.x; i < as.M * Wt * K; i += blockDim.x) {
       const int k = i % K, r = (i / K) % Wt, m = i / (K * Wt);
-      sm.Vs[(m * as.W + r) * (K + 1) + k] =
+      sm.Vs[(m * as.W + r) * v_stride(K) + k] =
           __ldcg(vst + ((size_t)m * as.N + w.s0 + r) * K + k);
     }
     if (threadIdx.x == 0) {
@@ -543,7 +771,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
       if (w.tile == 0) as.off[as.t_hi + 1] = c0;
     }
     cp_async_wait_all();
+    if (pb) {
+      if (threadIdx.x == 0 && !mbar_wait_bounded(sm.barP, parity_p, p)) s_abort = 1;
+      parity_p ^= 1u;
+    }
     __syncthreads();
+    if (s_abort) return;
     expectation(as, w, as.t_hi, sm.Ps, sm.Vs, ev_ptr(as, as.t_hi));
     publish(p.flags + as.flag_base + w.tile, 1);
     __syncthreads();
@@ -552,27 +785,43 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   for (int g = 0; g < p.n_steps; ++g) {
     for (int it = i0; it < i1; ++it) {
       const WorkItem w = p.items[it];
-      const AssetDev& as = p.assets[w.asset];
+      if (w.asset != cur_asset) {
+        load_asset(w.asset);
+        cur_asset = w.asset;
+      }
+      const AssetDev& as = s_as;
       if (g > as.t_hi - as.t_lo) continue;
-      sm.Ccol = sm.Ecol + as.M * as.rs;
-      if (!item_stage<R>(p, as, w, it, g, sm, parity)) return;
+      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p)) return;
       publish(p.flags + as.flag_base + w.tile, g + 2);
+      item_outputs(p, as, w, as.t_hi - g, sm);
     }
   }
 }
 
-// rho_t[k] = sum_k2 trans[t][k][k2] in double, for every asset of a launch
+// Instance preparation, per asset of a launch: rho_t[k] = sum_k2 P_t[k][k2]
+// in double, and ptrans[t][k2][k] = P_t[k][k2] with rows padded to
+// p_stride(K) (zeros), written in output order.
 __global__ void rowsum_kernel(const AssetDev* assets, const float* trans) {
   const AssetDev& as = assets[blockIdx.y];
-  const int K = as.K;
+  const int K = as.K, Kpt = p_stride(K);
   const long long rows = (long long)as.T * K;
   const float* P = trans + as.off_trans;
-  double* rho = as.rho;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
-       r += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long r = first; r < rows; r += stride) {
     double acc = 0.0;
     for (int k2 = 0; k2 < K; ++k2) acc += (double)__ldg(P + r * K + k2);
-    rho[r] = acc;
+    as.rho[r] = acc;
+  }
+  if (as.ptrans) {
+    const long long n = rows * Kpt;  // [T][K][Kpt]
+    for (long long i = first; i < n; i += stride) {
+      const long long tk2 = i / Kpt;
+      const int k = (int)(i - tk2 * Kpt);
+      const long long t = tk2 / K;
+      const int k2 = (int)(tk2 - t * K);
+      as.ptrans[i] = k < K ? __ldg(P + (t * K + k) * K + k2) : 0.f;
+    }
   }
 }
 
@@ -611,7 +860,7 @@ cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows,
                            const float* trans, cudaStream_t stream) {
   if (n_assets == 0) return cudaSuccess;
   const int block = 128;
-  const int gx = std::max(1, std::min(64, (max_rows + block - 1) / block));
+  const int gx = std::max(1, std::min(256, (max_rows + block - 1) / block));
   rowsum_kernel<<<dim3(gx, n_assets), block, 0, stream>>>(d_assets, trans);
   return cudaGetLastError();
 }
@@ -628,9 +877,10 @@ cudaError_t launch_ev_readout(const float* evp, const double* evoff, int M, int 
 cudaError_t launch_sweep(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
   switch (s.R) {
     case 4: return launch_R<4>(s, p, stream);
+    case 6: return launch_R<6>(s, p, stream);
     case 8: return launch_R<8>(s, p, stream);
+    case 10: return launch_R<10>(s, p, stream);
     case 12: return launch_R<12>(s, p, stream);
-    case 16: return launch_R<16>(s, p, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -638,9 +888,10 @@ cudaError_t launch_sweep(const SweepShape& s, const SweepParams& p, cudaStream_t
 int sweep_max_blocks_per_sm(int R, int block, size_t smem) {
   switch (R) {
     case 4: return max_blocks_R<4>(block, smem);
+    case 6: return max_blocks_R<6>(block, smem);
     case 8: return max_blocks_R<8>(block, smem);
+    case 10: return max_blocks_R<10>(block, smem);
     case 12: return max_blocks_R<12>(block, smem);
-    case 16: return max_blocks_R<16>(block, smem);
     default: return 0;
   }
 }
