@@ -79,7 +79,6 @@ struct esdp_ctx {
   std::vector<double*> d_evoff;   // per asset [T][K] EV_t - EV'_t
   std::vector<float*> d_refh;     // per asset [T+2] reference EV' entries
   std::vector<float*> d_ptrans;   // per asset [T][K][Kp4] transposed transition matrices
-  float* d_scratch = nullptr;     // readout staging (host mode), max MNK floats
   float* d_in_price = nullptr;    // host-mode input copies
   float* d_in_trans = nullptr;
   float* d_in_cost = nullptr;
@@ -626,11 +625,6 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
     if ((rc = dalloc(c, &pt, (size_t)a.T * a.K * p_stride(a.K)))) return rc;
     c->d_ptrans.push_back(pt);
   }
-  {
-    size_t mx = 0;
-    for (const esdp_asset& a : c->assets) mx = std::max(mx, mnk_of(a));
-    if ((rc = dalloc(c, &c->d_scratch, mx))) return rc;
-  }
   if (!(flags & ESDP_DEVICE_PTRS)) {
     if ((rc = dalloc(c, &c->d_in_price, c->n_price))) return rc;
     if ((rc = dalloc(c, &c->d_in_trans, c->n_trans))) return rc;
@@ -682,6 +676,14 @@ int esdp_solve(esdp_ctx* c, const float* price, const float* trans, const float*
   }
   int rc = run_plan(c, &c->main, dp, dt, dc, dm, dv, st);
   if (rc) return rc;
+  if (c->flags & ESDP_KEEP_EV) {
+    // the kept EV'_t become the reported EV_t (level added back, in double)
+    for (size_t id = 0; id < c->assets.size(); ++id) {
+      const esdp_asset& a = c->assets[id];
+      CK(launch_ev_restore(c->d_ev[id], c->d_evoff[id], a.T, a.n_modes * a.N, a.K, st),
+         "EV restore");
+    }
+  }
   c->last_price = dp;
   c->last_trans = dt;
   c->last_cost = dc;
@@ -759,13 +761,9 @@ int esdp_expected_value(esdp_ctx* c, int32_t asset, int32_t t, float* out, void*
   const size_t L = mnk_of(a);
   cudaStream_t st = (cudaStream_t)stream;
   const bool dev = (c->flags & ESDP_DEVICE_PTRS) != 0;
-  float* dst = dev ? out : c->d_scratch;
-  CK(launch_ev_readout(c->d_ev[asset] + (size_t)(t - 1) * L, c->d_evoff[asset] + (size_t)(t - 1) * a.K,
-                       a.n_modes, a.N, a.K, dst, st), "EV readout");
-  if (!dev) {
-    CK(cudaMemcpyAsync(out, dst, L * 4, cudaMemcpyDeviceToHost, st), "EV copy");
-    CK(cudaStreamSynchronize(st), "EV copy");
-  }
+  CK(cudaMemcpyAsync(out, c->d_ev[asset] + (size_t)(t - 1) * L, L * 4,
+                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st), "EV copy");
+  if (!dev) CK(cudaStreamSynchronize(st), "EV copy");
   return ESDP_OK;
 }
 
@@ -806,7 +804,6 @@ int esdp_bid_curves(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t*
   }
   HullParams hp{};
   hp.ev = c->d_ev[asset] + (size_t)(t0 - 1) * L;
-  hp.evoff = c->d_evoff[asset] + (size_t)(t0 - 1) * a.K;
   hp.n_t = n_t;
   hp.M = a.n_modes;
   hp.N = a.N;

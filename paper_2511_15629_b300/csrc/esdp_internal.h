@@ -115,14 +115,9 @@ int sweep_max_blocks_per_sm(int R, int block, size_t smem);
 // ptrans[t][k2][k] = trans[t][k][k2].
 cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows, const float* trans,
                            cudaStream_t stream);
-// out[m][s][k] = EV'_t + evoff_t[k] rounded to float (the reported EV_t).
-cudaError_t launch_ev_readout(const float* evp, const double* evoff, int M, int N, int K, float* out,
-                              cudaStream_t stream);
-
 // Bid-curve envelope kernel.
 struct HullParams {
-  const float* ev;   // EV'_t of stage t0 at ev, stage stride MNK, layout [M][N][K]
-  const double* evoff;  // [n_t][K]: EV_t = float(EV'_t + evoff)
+  const float* ev;   // EV_t of stage t0 at ev, stage stride MNK, layout [M][N][K]
   int n_t, M, N, K;
   double delta;      // SoC step (MWh): slopes in $ per MWh
   int* n_bp;         // [n_t][M][K]
@@ -130,6 +125,9 @@ struct HullParams {
   float* slope;      // [n_t][M][K][N]
 };
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream);
+// Kept EV'_t of n_t stages -> reported EV_t = float(EV'_t + evoff_t[k]), in place.
+cudaError_t launch_ev_restore(float* ev, const double* evoff, int n_t, int MN, int K,
+                              cudaStream_t stream);
 
 // Occupancy adjoint kernels.
 struct OccParams {

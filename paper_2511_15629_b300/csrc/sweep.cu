@@ -825,14 +825,6 @@ __global__ void rowsum_kernel(const AssetDev* assets, const float* trans) {
   }
 }
 
-__global__ void ev_readout_kernel(const float* evp, const double* evoff, int M, int N, int K,
-                                  float* out) {
-  const long long n = (long long)M * N * K;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = (float)((double)evp[i] + evoff[i % K]);
-}
-
 template <int R>
 cudaError_t launch_R(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
   auto fn = sweep_kernel<R>;
@@ -862,15 +854,6 @@ cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows,
   const int block = 128;
   const int gx = std::max(1, std::min(256, (max_rows + block - 1) / block));
   rowsum_kernel<<<dim3(gx, n_assets), block, 0, stream>>>(d_assets, trans);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ev_readout(const float* evp, const double* evoff, int M, int N, int K,
-                              float* out, cudaStream_t stream) {
-  const long long n = (long long)M * N * K;
-  const int block = 256;
-  const int grid = (int)std::min<long long>(1184, (n + block - 1) / block);
-  ev_readout_kernel<<<std::max(grid, 1), block, 0, stream>>>(evp, evoff, M, N, K, out);
   return cudaGetLastError();
 }
 
