@@ -15,7 +15,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -49,60 +48,57 @@ def parse():
 # ------------------------------------------------------------------ helpers
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle sampling during the timed region."""
+    """SM clock and clock-event reasons sampled through NVML every few
+    milliseconds while the timed region runs (falls back to nvidia-smi)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.period = period_s
+        self.samples = []
+        self._stop = threading.Event()
+        self._max = None
+
+    def _loop(self, nv, h):
+        while not self._stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                try:
+                    rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                except AttributeError:
+                    rs = nv.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+                self.samples.append((sm, rs))
+            except Exception:
+                pass
+            time.sleep(self.period)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self._t = threading.Thread(target=self._read, daemon=True)
+            import pynvml as nv
+            nv.nvmlInit()
+            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            self._max = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            self._t = threading.Thread(target=self._loop, args=(nv, h), daemon=True)
             self._t.start()
-        except FileNotFoundError:
-            self.proc = None
+        except Exception:
+            self._t = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *exc):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=2)
 
     def summary(self) -> dict:
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self._max, "reasons": [], "samples": 0}
+        reasons = sorted(n for n, bit in self.REASONS.items()
+                         if any(r & bit for _, r in self.samples))
+        return {"sm_mhz": statistics.median(s for s, _ in self.samples), "sm_max_mhz": self._max,
+                "sm_mhz_min": min(s for s, _ in self.samples), "reasons": reasons,
+                "samples": len(self.samples)}
 
 
 def measured_peaks() -> dict:
@@ -111,6 +107,21 @@ def measured_peaks() -> dict:
         with open(p) as f:
             return json.load(f)
     return {}
+
+
+def measured_traffic():
+    """DRAM bytes per sweep launch from the committed ncu capture, or None
+    when the kernel source has changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_config2.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
+            return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
 def alu_peak_evals(n_sm: int, mhz: float) -> float:
@@ -191,11 +202,13 @@ def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
         step(None)
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(marks + 1)] for _ in range(steps)]
+    torch.cuda.nvtx.range_push("esdp_steps")  # the timed region, for ncu --nvtx-include
     for i in range(steps):
         with torch.cuda.stream(stream):
             flush()
             step(ev[i])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     per_mark = [0.0] * marks
     for i in range(steps):
         for j in range(marks):
@@ -265,7 +278,7 @@ def run_esdp(args, rank, world):
     peak = alu_peak_evals(n_sm, f_max)
     clocks = clk.summary()
     roof = {"bound": "alu", "achieved": sweep_evals_s / 1e9, "peak": peak / 1e9,
-            "unit": "Gevals/s", "frac": sweep_evals_s / peak, "traffic": None,
+            "unit": "Gevals/s", "frac": sweep_evals_s / peak, "traffic": measured_traffic(),
             "kernel": "sweep_kernel", "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x "
             f"{f_max:.0f} MHz / 2 ops per evaluation (max clock)"}
     if clocks.get("sm_mhz"):

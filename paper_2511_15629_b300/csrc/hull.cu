@@ -206,15 +206,44 @@ __global__ void __launch_bounds__(32 * kSeg) hull_kernel(const HullParams p) {
   }
 }
 
-// EV_t = float(EV'_t + evoff_t[k]) for every kept stage, in place
-__global__ void ev_restore_kernel(float* ev, const double* evoff, int n_t, int MN, int K) {
-  const long long per = (long long)MN * K;
-  const long long n = per * n_t;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long t = i / per;
-    const int k = (int)(i % K);
-    ev[i] = (float)((double)ev[i] + evoff[t * K + k]);
+// Reported EV_t = EV'_t + evoff_t[k] for every kept stage, in place, as a
+// float32 compensated sum: the level is split into hi + lo floats and the
+// rounding error of EV' + hi (TwoSum) is carried into the final addition.
+__device__ __forceinline__ float add_level(float a, float hi, float lo) {
+  const float s = __fadd_rn(a, hi);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(hi, bb));
+  return __fadd_rn(s, __fadd_rn(err, lo));
+}
+
+// grid.y = stage; rows of K values, float4 when K is a multiple of 4
+__global__ void ev_restore_kernel(float* ev, const double* evoff, int MN, int K) {
+  __shared__ float s_hi[128], s_lo[128];
+  const int t = blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double o = evoff[(size_t)t * K + k];
+    s_hi[k] = (float)o;
+    s_lo[k] = (float)(o - (double)(float)o);
+  }
+  __syncthreads();
+  float* e = ev + (size_t)t * MN * K;
+  const int n = MN * K;
+  if ((K & 3) == 0) {
+    float4* e4 = reinterpret_cast<float4*>(e);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n / 4; i += gridDim.x * blockDim.x) {
+      const int k = (4 * i) % K;
+      float4 v = e4[i];
+      v.x = add_level(v.x, s_hi[k], s_lo[k]);
+      v.y = add_level(v.y, s_hi[k + 1], s_lo[k + 1]);
+      v.z = add_level(v.z, s_hi[k + 2], s_lo[k + 2]);
+      v.w = add_level(v.w, s_hi[k + 3], s_lo[k + 3]);
+      e4[i] = v;
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int k = i % K;
+      e[i] = add_level(e[i], s_hi[k], s_lo[k]);
+    }
   }
 }
 
@@ -229,12 +258,12 @@ cudaError_t launch_hull(const HullParams& p, cudaStream_t stream) {
 
 cudaError_t launch_ev_restore(float* ev, const double* evoff, int n_t, int MN, int K,
                               cudaStream_t stream) {
-  const long long n = (long long)MN * K * n_t;
-  if (n == 0) return cudaSuccess;
+  const long long n = (long long)MN * K;
+  if (n == 0 || n_t == 0) return cudaSuccess;
   const int block = 256;
-  const long long want = (n + block - 1) / block;
-  const int grid = (int)(want < 148 * 16 ? want : 148 * 16);
-  ev_restore_kernel<<<grid, block, 0, stream>>>(ev, evoff, n_t, MN, K);
+  const long long per = ((K & 3) == 0 ? n / 4 : n);
+  const int gx = (int)((per + block - 1) / block < 64 ? (per + block - 1) / block : 64);
+  ev_restore_kernel<<<dim3(gx, n_t), block, 0, stream>>>(ev, evoff, MN, K);
   return cudaGetLastError();
 }
 
