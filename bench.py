@@ -47,9 +47,38 @@ def parse():
 
 # ------------------------------------------------------------------ helpers
 
+class _Nvml:
+    """Minimal ctypes binding of the driver's NVML (no Python package needed)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, index: int):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML device")
+        self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self, maxclock=False) -> int:
+        v = self.c.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if maxclock else self.lib.nvmlDeviceGetClockInfo
+        fn(self.h, self.c.c_int(self.CLOCK_SM), self.c.byref(v))
+        return int(v.value)
+
+    def reasons(self) -> int:
+        v = self.c.c_ulonglong()
+        self._reasons(self.h, self.c.byref(v))
+        return int(v.value)
+
+
 class ClockSampler:
     """SM clock and clock-event reasons sampled through NVML every few
-    milliseconds while the timed region runs (falls back to nvidia-smi)."""
+    milliseconds while the timed region runs."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
@@ -60,30 +89,25 @@ class ClockSampler:
         self.samples = []
         self._stop = threading.Event()
         self._max = None
+        self._t = None
+        self.error = None
 
-    def _loop(self, nv, h):
+    def _loop(self, nv):
         while not self._stop.is_set():
             try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                try:
-                    rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                except AttributeError:
-                    rs = nv.nvmlDeviceGetCurrentClocksThrottleReasons(h)
-                self.samples.append((sm, rs))
+                self.samples.append((nv.clock(), nv.reasons()))
             except Exception:
                 pass
             time.sleep(self.period)
 
     def __enter__(self):
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            h = nv.nvmlDeviceGetHandleByIndex(self.index)
-            self._max = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-            self._t = threading.Thread(target=self._loop, args=(nv, h), daemon=True)
+            nv = _Nvml(self.index)
+            self._max = nv.clock(maxclock=True)
+            self._t = threading.Thread(target=self._loop, args=(nv,), daemon=True)
             self._t.start()
-        except Exception:
-            self._t = None
+        except Exception as ex:
+            self.error = f"{type(ex).__name__}: {ex}"
         return self
 
     def __exit__(self, *exc):
@@ -93,7 +117,8 @@ class ClockSampler:
 
     def summary(self) -> dict:
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self._max, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": self._max, "reasons": [], "samples": 0,
+                    "error": self.error}
         reasons = sorted(n for n, bit in self.REASONS.items()
                          if any(r & bit for _, r in self.samples))
         return {"sm_mhz": statistics.median(s for s, _ in self.samples), "sm_max_mhz": self._max,

@@ -363,7 +363,6 @@ __device__ __forceinline__ void publish(int* flag, int v) {
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    __threadfence();
     st_release(flag, v);
   }
 }
@@ -413,10 +412,39 @@ struct Smem {
   uint64_t* barP;  // transposed P bulk copy
 };
 
+// Payoff columns of each mode: (e_a, -(cost_a + switch)), -inf padding to a
+// multiple of R per action segment; the payoff r = price*e_a - cost_a is
+// formed in the max-plus itself.  They depend on the asset only.
+template <int R>
+__device__ void build_columns(const SweepParams& p, const AssetDev& as, float2* EC) {
+  const int M = as.M, rs = as.rs;
+  const float NEG = -CUDART_INF_F;
+  const float* cost = p.cost + as.off_cost;
+  for (int i = threadIdx.x; i < M * rs; i += blockDim.x) {
+    const int m = i / rs, j = i - m * rs;
+    Seg g0, g1;
+    segments(as, m, g0, g1);
+    const int L0p = round_up(g0.len, R);
+    int a = -1;
+    float sw = 0.f;
+    if (j < L0p) {
+      if (j < g0.len) {
+        a = g0.a0 + j;
+        sw = g0.sw;
+      }
+    } else if (j - L0p < g1.len) {
+      a = g1.a0 + (j - L0p);
+      sw = g1.sw;
+    }
+    EC[i] = a >= 0 ? make_float2(__ldg(as.e + a), -__ldg(cost + a) - sw) : make_float2(0.f, NEG);
+  }
+}
+
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
-                           int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p) {
+                           int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p,
+                           bool p_pref) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
@@ -426,7 +454,9 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
 
   // 0. prefetch the inputs of the stage
-  const bool p_bulk = t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP);
+  // (the bulk copy of P_{t-1}^T may already be in flight: issued right after
+  // the previous stage's release)
+  const bool p_bulk = p_pref || (t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP));
   float lam_k = 0.f;
   double rho_k = 0.0, c_next = 0.0;
   if (tid < K) {
@@ -435,29 +465,6 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   }
   if (tid == 0) c_next = p.item_c[it];
 
-  // payoff columns of each mode: (e_a, -(cost_a + switch)), -inf padding;
-  // the payoff r = price*e_a - cost_a is formed in the max-plus itself
-  {
-    const float* cost = p.cost + as.off_cost;
-    for (int i = tid; i < M * rs; i += nth) {
-      const int m = i / rs, j = i - m * rs;
-      Seg g0, g1;
-      segments(as, m, g0, g1);
-      const int L0p = round_up(g0.len, R);
-      int a = -1;
-      float sw = 0.f;
-      if (j < L0p) {
-        if (j < g0.len) {
-          a = g0.a0 + j;
-          sw = g0.sw;
-        }
-      } else if (j - L0p < g1.len) {
-        a = g1.a0 + (j - L0p);
-        sw = g1.sw;
-      }
-      sm.EC[i] = a >= 0 ? make_float2(__ldg(as.e + a), -__ldg(cost + a) - sw) : make_float2(0.f, NEG);
-    }
-  }
   // 1. neighbours
   if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
 
@@ -747,7 +754,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
   };
-  int cur_asset = -1;
+  int cur_asset = -1, cols_asset = -1;
+  bool pref = false;
 
   // prologue: EV'_{t_hi} = P_{t_hi} V'_{t_hi+1} for the item's rows
   for (int it = i0; it < i1; ++it) {
@@ -791,8 +799,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
       }
       const AssetDev& as = s_as;
       if (g > as.t_hi - as.t_lo) continue;
-      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p)) return;
+      if (w.asset != cols_asset) {
+        build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
+        cols_asset = w.asset;
+      }
+      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, pref)) return;
       publish(p.flags + as.flag_base + w.tile, g + 2);
+      // start the next stage's P^T copy now when that stage is of the same
+      // asset: its latency then overlaps the output stores and the wait
+      {
+        const int nit = it + 1 < i1 ? it + 1 : i0;
+        const int ng = it + 1 < i1 ? g : g + 1;
+        const int nt = as.t_hi - ng;
+        pref = as.ptrans != nullptr && ng < p.n_steps && p.items[nit].asset == w.asset &&
+               ng <= as.t_hi - as.t_lo && nt > as.t_lo;
+        if (pref) load_trans_async(p, as, nt - 1, sm.Ps, sm.barP);
+      }
       item_outputs(p, as, w, as.t_hi - g, sm);
     }
   }
