@@ -417,3 +417,46 @@ def test_autotune_keeps_results():
     np.testing.assert_array_equal(V1, V1b)
     info = s.launch_info()
     assert info["grid"] >= 1 and info["rows_per_thread"] in (4, 6, 8, 10, 12)
+
+
+# ------------------------------------------------- bid-curve exact predicate
+
+def _hull_gpu_vs_oracle(inst):
+    s, V1 = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, slope = s.bid_curves(0, 1, inst.T + 1)
+    ev = np.stack([s.expected_value(0, t) for t in range(1, inst.T + 1)])
+    ref_n, ref_idx, _ = O.bid_curves(inst, ev)
+    np.testing.assert_array_equal(n_bp, ref_n)
+    for t in range(inst.T):
+        for m in range(inst.n_modes):
+            for k in range(inst.K):
+                n = n_bp[t, m, k]
+                np.testing.assert_array_equal(idx[t, m, k, :n], ref_idx[t, m, k, :n])
+    return ev
+
+
+def test_bid_curves_exact_collinear():
+    """Zero prices and costs with a linear terminal value: EV is exactly linear
+    in SoC in float32 (small integers), every middle point is collinear and
+    the orientation test must take its exact route.  (The level offsets and
+    the float32 row sums perturb a few values by an ulp.)"""
+    inst = I.random_instance(80, 3, 300, 4, 5, 5, 1, cost="zero", terminal="linear",
+                             s_max=299.0, eta=(1.0, 1.0))
+    inst.price[:] = 0
+    inst.terminal[:] = (np.arange(inst.N, dtype=np.float32) * np.float32(0.5))[None, :, None]
+    ev = _hull_gpu_vs_oracle(inst).astype(np.float64)
+    # most consecutive triples are exactly collinear (differences are exact
+    # in double for these float32 values), so the exact route decided them
+    d = np.diff(ev, axis=2)
+    assert np.mean(d[:, :, 1:, :] == d[:, :, :-1, :]) > 0.5
+
+
+def test_bid_curves_wide_dynamic_range():
+    """Values spanning many binary orders of magnitude (tiny next to large)
+    exercise the double route of the exact orientation test."""
+    inst = I.random_instance(81, 2, 200, 3, 3, 3, 1, cost="zero", terminal="random")
+    rng = np.random.default_rng(5)
+    term = rng.uniform(-1, 1, size=inst.terminal.shape) * 10.0 ** rng.integers(-12, 6, size=inst.terminal.shape)
+    inst.terminal[:] = term.astype(np.float32)
+    inst.price[:] = np.float32(1e-6)
+    _hull_gpu_vs_oracle(inst)
