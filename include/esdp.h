@@ -117,6 +117,13 @@ int esdp_expected_value(esdp_ctx* ctx, int32_t asset, int32_t t, float* out, voi
 int esdp_bid_curves(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
                     int32_t* bp_idx, float* slope, void* stream);
 
+/* Objective J = sum_k mu0[k] V_1[0][s0][k] (mode 0, initial SoC index s0 of
+ * the asset) from the V_1 of the last esdp_solve, summed in double on the
+ * device.  mu0 [K] is the initial price-state distribution; J [1] (double).
+ * Host mode blocks; device mode queues one tiny kernel on `stream`.
+ * ESDP_ESTATE before the first solve, ESDP_EINVAL on a bad asset index. */
+int esdp_objective(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, void* stream);
+
 /* Objective J = sum_k mu0[k] V_1[0][s0][k] and its sensitivities by a
  * forward pass of the state-occupancy distribution under the stored argmax
  * policy (envelope theorem on eq. 5-6; exact away from ties).  With

@@ -84,6 +84,8 @@ struct esdp_ctx {
   float* d_in_cost = nullptr;
   float* d_in_terminal = nullptr;
   float* d_v1 = nullptr;          // host-mode V1
+  float* d_obj_mu = nullptr;      // host-mode esdp_objective staging: mu0 (max K floats)
+  double* d_obj_J = nullptr;      // ... and J
   int* d_status = nullptr;
   // inputs of the last solve (device pointers)
   const float* last_price = nullptr;
@@ -633,6 +635,10 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
   }
   // V_1 lands here when the caller passes no output (the gradient needs it)
   if ((rc = dalloc(c, &c->d_v1, c->n_v1))) return rc;
+  int k_max = 1;
+  for (const esdp_asset& a : c->assets) k_max = std::max(k_max, (int)a.K);
+  if ((rc = dalloc(c, &c->d_obj_mu, (size_t)k_max))) return rc;
+  if ((rc = dalloc(c, &c->d_obj_J, (size_t)1))) return rc;
   std::vector<int> ids(c->assets.size());
   std::iota(ids.begin(), ids.end(), 0);
   if ((rc = plan_default(c, ids, &c->main))) return rc;
@@ -993,6 +999,28 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   release();
   if (e != cudaSuccess) return cuda_fail(c, e, "grad");
   if (status) return fail(c, status, "device reported status %d in the adjoint", status);
+  return ESDP_OK;
+}
+
+extern "C" int esdp_objective(esdp_ctx* c, int32_t asset, const float* mu0, double* J,
+                              void* stream) {
+  if (!c || !mu0 || !J) return ESDP_EINVAL;
+  if (asset < 0 || asset >= (int32_t)c->assets.size())
+    return fail(c, ESDP_EINVAL, "asset index %d out of range", asset);
+  if (!c->solved) return fail(c, ESDP_ESTATE, "no solve has completed");
+  const esdp_asset& a = c->assets[asset];
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* v1 = c->last_v1 + c->off_v1[asset];
+  if (c->flags & ESDP_DEVICE_PTRS) {
+    objective_kernel<<<1, 32, 0, st>>>(v1, mu0, a.K, a.s0, J);
+    CK(cudaGetLastError(), "objective");
+    return ESDP_OK;
+  }
+  CK(cudaMemcpyAsync(c->d_obj_mu, mu0, (size_t)a.K * 4, cudaMemcpyHostToDevice, st), "H2D");
+  objective_kernel<<<1, 32, 0, st>>>(v1, c->d_obj_mu, a.K, a.s0, c->d_obj_J);
+  CK(cudaGetLastError(), "objective");
+  CK(cudaMemcpyAsync(J, c->d_obj_J, 8, cudaMemcpyDeviceToHost, st), "D2H");
+  CK(cudaStreamSynchronize(st), "objective");
   return ESDP_OK;
 }
 

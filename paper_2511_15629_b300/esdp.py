@@ -35,7 +35,7 @@ ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
-           "esdp_grad", "esdp_autotune", "esdp_status", "esdp_launch_info", "esdp_destroy",
+           "esdp_objective", "esdp_grad", "esdp_autotune", "esdp_status", "esdp_launch_info", "esdp_destroy",
            "esdp_last_error", "esdp_version"]
 
 
@@ -73,6 +73,7 @@ def load_library():
     lib.esdp_policy.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_expected_value.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_bid_curves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.esdp_objective.argtypes = [vp, i32, vp, vp, vp]
     lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
     lib.esdp_status.argtypes = [vp, vp]
@@ -238,6 +239,18 @@ class Solver:
                                               p(idx, np.int32), p(slope, np.float32),
                                               _stream(stream)))
         return n_bp, idx, slope
+
+    def objective(self, asset: int, mu0, J=None, stream=None):
+        """J = sum_k mu0[k] V_1[0][s0][k] of the last solve (double)."""
+        if not self.device:
+            mu0 = np.ascontiguousarray(mu0, dtype=np.float32)
+            J = np.zeros(1, np.float64) if J is None else J
+            ptr = _host_ptr
+        else:
+            ptr = lambda a, dt: _dev_ptr(a)
+        self._check(self._lib.esdp_objective(self._ctx, asset, ptr(mu0, np.float32),
+                                             ptr(J, np.float64), _stream(stream)))
+        return J
 
     def grad(self, asset: int, mu0, J=None, d_price=None, d_trans=None, d_eta=None, stream=None):
         inst = self.instances[asset]

@@ -460,3 +460,59 @@ def test_bid_curves_wide_dynamic_range():
     inst.terminal[:] = term.astype(np.float32)
     inst.price[:] = np.float32(1e-6)
     _hull_gpu_vs_oracle(inst)
+
+
+# ------------------------------------------------- torch.autograd.Function
+
+def test_autograd_objective_matches_oracle_adjoint():
+    import torch
+    from paper_2511_15629_b300.autograd import StorageObjective
+    inst = I.random_instance(53, 6, 25, 3, 3, 3, 1, neg_prob=0.2, cost="linear")
+    inst.s0 = 12
+    f = StorageObjective(inst)
+    dev = f.device
+    price = torch.tensor(inst.price, device=dev, requires_grad=True)
+    trans = torch.tensor(inst.trans, device=dev, requires_grad=True)
+    eta_c = torch.tensor(inst.eta_c, dtype=torch.float64, requires_grad=True)
+    eta_d = torch.tensor(inst.eta_d, dtype=torch.float64, requires_grad=True)
+    J = f(price, trans, eta_c, eta_d)
+    # another solve in between: backward must recompute the first one
+    J_other = f(price.detach() * 2, trans.detach())
+    J.backward()
+    r = O.solve(inst, keep_V=True, nthreads=NTHREADS)
+    assert float(J.detach()) == pytest.approx(O.objective(inst, r["V1"]), rel=VTOL)
+    assert float(J_other) != pytest.approx(float(J.detach()), rel=1e-3)
+    occ = O.occupancy(inst, r["policy"], r["V"])
+    for g, key in ((price.grad, "d_price"), (trans.grad, "d_trans"),
+                   (eta_c.grad, "d_eta_c"), (eta_d.grad, "d_eta_d")):
+        ref = np.atleast_1d(occ[key])
+        got = g.detach().cpu().numpy().astype(np.float64).reshape(ref.shape)
+        err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-12)
+        assert err <= 1e-4, f"{key}: rel error {err:.3e}"
+    # central differences of the GPU forward in eta_c (float32 values: the
+    # quotient carries ~1e-7 |J| / h of noise)
+    h = 1e-4
+    with torch.no_grad():
+        jp = float(f(price, trans, eta_c + h, eta_d))
+        jm = float(f(price, trans, eta_c - h, eta_d))
+    fd = (jp - jm) / (2 * h)
+    assert fd == pytest.approx(float(eta_c.grad), rel=2e-2, abs=1e-7 * abs(float(J.detach())) / h)
+
+
+def test_autograd_checkpointed_int16():
+    import torch
+    from paper_2511_15629_b300.autograd import StorageObjective
+    inst = I.random_instance(54, 40, 120, 5, 9, 9, 2, neg_prob=0.2, switch_cost=3.0)
+    inst.s0 = 60
+    inst.ckpt_every = 7
+    inst.policy_bytes = 2
+    f = StorageObjective(inst)
+    price = torch.tensor(inst.price, device=f.device, requires_grad=True)
+    trans = torch.tensor(inst.trans, device=f.device, requires_grad=True)
+    f(price, trans).backward()
+    s, _ = solve_gpu(inst)
+    J, dp, dt, de = s.grad(0, inst.mu0)
+    # same adjoint; the occupancy sums use atomics, so the order of the
+    # double additions (and the last float32 bit) may differ between runs
+    np.testing.assert_allclose(price.grad.cpu().numpy(), dp, rtol=1e-6, atol=1e-6 * np.abs(dp).max())
+    np.testing.assert_allclose(trans.grad.cpu().numpy(), dt, rtol=1e-6, atol=1e-6 * np.abs(dt).max())
