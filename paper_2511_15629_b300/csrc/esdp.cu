@@ -173,7 +173,7 @@ struct AssetChoice {
 };
 
 size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R) {
-  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R, ch.parts).bytes;
+  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R).bytes;
 }
 
 int n_chunks_min(const esdp_asset& a, int R) {
@@ -199,12 +199,11 @@ bool choose_asset(const esdp_asset& a, int R, int block, double cta_share, Asset
     ch.n_tiles = (a.N + ch.W - 1) / ch.W;
     ch.rows = ch.W + a.A + R;
     ch.rs = (a.A + 2 * R) | 1;
-    const int pmax = std::max(1, std::min(block / (KM * nb), n_chunks_min(a, R) / 2));
-    ch.parts = std::max(1, pmax);
+    ch.parts = pick_parts(KM * nb, block, n_chunks_min(a, R));
+    if (ch.parts < 1) continue;
     const int dmax = std::max(a.D_dis, a.D_chg);
     const int nw = 2 * ((dmax + ch.W - 1) / ch.W) + 1;
     if (nw + 1 > block) continue;  // one thread per neighbour wait + the reference tile
-    while (smem_need(a, ch, R) > kSmemLimit && ch.parts > 1) --ch.parts;
     if (smem_need(a, ch, R) > kSmemLimit) continue;
     *out = ch;
     return true;
@@ -246,7 +245,7 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
                   "asset %d (K=%d, modes=%d, A=%d) does not fit a %d-thread tile in shared memory",
                   ids[j], a.K, a.n_modes, a.A, block);
     {
-      const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R, ch[j].parts);
+      const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R);
       const long long endX = (long long)(L.bytes / sizeof(float));
       need_E = std::max<long long>(need_E, L.Rt - L.E);
       need_R = std::max<long long>(need_R, L.C - L.Rt);

@@ -86,7 +86,7 @@ struct SweepSmem {
   int E, Rt, C, V, P, X;
   size_t bytes;
 };
-inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R, int parts) {
+inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R) {
   auto al = [](long long x) { return (int)((x + 31) / 32 * 32); };
   const int rows = W + A + R, rs = (A + 2 * R) | 1;
   SweepSmem s;
@@ -96,8 +96,23 @@ inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R, int parts)
   s.V = s.C + al(2LL * M * rs);
   s.P = s.V + al((long long)M * W * v_stride(K));
   s.X = s.P + al((long long)K * p_stride(K));
-  s.bytes = (size_t)(s.X + al(2LL * parts * M * W * K)) * sizeof(float);
+  s.bytes = (size_t)(s.X + al((long long)M * W * K)) * sizeof(float);  // argmax indices
   return s;
+}
+
+// Threads of the max-plus phase: cells (price-state pairs x row blocks x
+// modes) laid out over warps of 32/G cell slots x G action parts.
+inline int maxplus_threads(int cells, int G) {
+  const int L = 32 / G;
+  return (cells + L - 1) / L * 32;
+}
+
+// The action split: the largest power of two G <= 32, at most half the
+// chunks of R actions, whose max-plus threads fit the block; 0 if none does.
+inline int pick_parts(int cells, int block, int chunks) {
+  for (int G = 32; G >= 1; G >>= 1)
+    if (G <= (chunks / 2 > 1 ? chunks / 2 : 1) && maxplus_threads(cells, G) <= block) return G;
+  return 0;
 }
 
 // Launch shape of one sweep.

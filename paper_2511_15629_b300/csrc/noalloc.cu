@@ -119,12 +119,10 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
     rs = (a.A + 2 * R) | 1;
     const int reach = (std::max(a.D_dis, a.D_chg) + W - 1) / W;
     if (2 * reach + 2 > block) continue;
-    parts = std::max(1, std::min(block / (KM * nb), chunks_min(a, R) / 2));
-    for (; parts >= 1; --parts) {
-      L = sweep_smem_layout(M, K, W, a.A, R, parts);
-      if (L.bytes <= kSmemLimit) break;
-    }
-    if (parts >= 1 && L.bytes <= kSmemLimit) break;
+    parts = pick_parts(KM * nb, block, chunks_min(a, R));
+    if (parts < 1) continue;
+    L = sweep_smem_layout(M, K, W, a.A, R);
+    if (L.bytes <= kSmemLimit) break;
   }
   if (nb < 1) return msg(err, err_len, ESDP_EINVAL, "no launch shape fits shared memory");
   if (tiles > kNoAllocMaxItems) {

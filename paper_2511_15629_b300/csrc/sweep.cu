@@ -61,6 +61,17 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 
 // Two independent round-to-nearest float32 operations per instruction
 // (one per price state of a pair); each lane equals the scalar operation.
+// (v, c) of this lane or of lane ^ d: the larger value, on equal values the
+// smaller chunk index (-1, no feasible action, compares as the largest)
+__device__ __forceinline__ void merge_part(float& v, int& c, int d) {
+  const float ov = __shfl_xor_sync(0xffffffffu, v, d);
+  const int oc = __shfl_xor_sync(0xffffffffu, c, d);
+  if (ov > v || (ov == v && (unsigned)oc < (unsigned)c)) {
+    v = ov;
+    c = oc;
+  }
+}
+
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
   unsigned long long x = *reinterpret_cast<unsigned long long*>(&a);
   unsigned long long y = *reinterpret_cast<unsigned long long*>(&b), r;
@@ -440,6 +451,47 @@ __device__ void build_columns(const SweepParams& p, const AssetDev& as, float2* 
   }
 }
 
+// One chunk of R actions for R rows and a pair of price states.  `eb` points
+// at the EV pair of the chunk's first action for the first row (rows and
+// actions both step by one EV row), `ecp` at the chunk's payoff columns.
+// Each running maximum takes the chunk's R candidates in one chain of 3-input
+// maxima; the chunk index is recorded where a maximum strictly rises, so the
+// earliest chunk that attains it is kept.
+template <int R>
+__device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const float2* ecp,
+                                              float2 lam, int c, float2 (&best)[R], int (&bx)[R],
+                                              int (&by)[R]) {
+  float2 wv[2 * R - 1];
+#pragma unroll
+  for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
+  float2 rr[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const float2 e = ecp[i];
+    rr[i] = fma2(lam, make_float2(e.x, e.x), make_float2(e.y, e.y));
+  }
+  float2 nm[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const float2 x = add2(rr[0], wv[j]), y = add2(rr[1], wv[j + 1]);
+    nm[j] = make_float2(max3f(best[j].x, x.x, y.x), max3f(best[j].y, x.y, y.y));
+  }
+#pragma unroll
+  for (int i = 2; i < R; i += 2) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float2 x = add2(rr[i], wv[i + j]), y = add2(rr[i + 1], wv[i + 1 + j]);
+      nm[j] = make_float2(max3f(nm[j].x, x.x, y.x), max3f(nm[j].y, x.y, y.y));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    if (nm[j].x > best[j].x) bx[j] = c;
+    if (nm[j].y > best[j].y) by[j] = c;
+    best[j] = nm[j];
+  }
+}
+
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
@@ -447,8 +499,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
                            bool p_pref) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
-            nwarps = nth >> 5;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const float NEG = -CUDART_INF_F;
   const bool tma = (K & 3) == 0;
   const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
@@ -533,26 +584,32 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   __syncthreads();
   if (*(volatile int*)sm.abort) return false;
 
-  // 3. banded max-plus: a thread owns R consecutive rows of one mode and a
-  //    pair of price states; it slides a register window of EV pairs over the
-  //    action band, two evaluations per packed add and per 3-input max
-  const int MWK = M * W * K;
-  int* Xi = reinterpret_cast<int*>(sm.Xs + (size_t)as.parts * MWK);
+  // 3. banded max-plus.  A cell is (pair of price states, block of R rows,
+  //    mode); its chunks of R actions are split into G = parts contiguous
+  //    ranges.  A warp holds L = 32/G cells in each of the G ranges (lane =
+  //    cell slot + L * part), so the parts of a cell meet in one warp and are
+  //    merged by shuffles.  Each lane slides a register window of EV pairs
+  //    over its chunks: two evaluations per packed add and per 3-input max.
   const int Kh = Ke >> 1;
-  const int nact = Kh * as.nb * M * as.parts;
-  if (tid < nact) {
-    const int kp = tid % Kh;
-    int q = tid / Kh;
+  const int G = as.parts, lgL = 5 - (31 - __clz(G)), L = 32 >> (31 - __clz(G));
+  const int ncell = Kh * as.nb * M;
+  int* Xi = reinterpret_cast<int*>(sm.Xs);
+  const int Wt = w.s1 - w.s0, Kv = v_stride(K);
+  if (warp * L < ncell) {  // warp-uniform: every lane takes part in the shuffles
+    const int part = lane >> lgL;
+    const int cell = warp * L + (lane & (L - 1));
+    const bool active = cell < ncell;
+    const int cc = active ? cell : 0;
+    const int kp = cc % Kh;
+    int q = cc / Kh;
     const int b = q % as.nb;
-    q /= as.nb;
-    const int m = q % M;
-    const int part = q / M;
+    const int m = q / as.nb;
     const int k0 = 2 * kp;
     Seg g0, g1;
     segments(as, m, g0, g1);
     const int n0 = round_up(g0.len, R) / R;
     const int nc = n0 + round_up(g1.len, R) / R;
-    const int c_lo = part * nc / as.parts, c_hi = (part + 1) * nc / as.parts;
+    const int c_lo = part * nc / G, c_hi = active ? (part + 1) * nc / G : c_lo;
     const float2* ec = sm.EC + m * rs;
     const float2 lam = make_float2(sm.lam[k0], sm.lam[k0 + 1]);
     float2 best[R];
@@ -563,7 +620,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
       bx[j] = -1;
       by[j] = -1;
     }
-    for (int c = c_lo; c < c_hi; ++c) {
+    auto chunk = [&](int c) {
       const bool second = c >= n0;
       const int u0 = (second ? c - n0 : c) * R;
       const int a0 = second ? g1.a0 : g0.a0;
@@ -571,102 +628,65 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
       const int toff = second ? n0 * R : 0;
       const float2* eb =
           reinterpret_cast<const float2*>(sm.Es + ((size_t)src * rows + b * R + a0 + u0) * Ke) + kp;
-      float2 wv[2 * R - 1];
-#pragma unroll
-      for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
-      float2 rr[R];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const float2 e = ec[toff + u0 + i];
-        rr[i] = fma2(lam, make_float2(e.x, e.x), make_float2(e.y, e.y));
-      }
-      float2 cm[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const float2 x = add2(rr[0], wv[j]), y = add2(rr[1], wv[j + 1]);
-        cm[j] = make_float2(fmaxf(x.x, y.x), fmaxf(x.y, y.y));
-      }
-#pragma unroll
-      for (int i = 2; i < R; i += 2) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const float2 x = add2(rr[i], wv[i + j]), y = add2(rr[i + 1], wv[i + 1 + j]);
-          cm[j] = make_float2(max3f(cm[j].x, x.x, y.x), max3f(cm[j].y, x.y, y.y));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        if (cm[j].x > best[j].x) {
-          best[j].x = cm[j].x;
-          bx[j] = c;
-        }
-        if (cm[j].y > best[j].y) {
-          best[j].y = cm[j].y;
-          by[j] = c;
-        }
+      maxplus_chunk<R>(eb, Kh, ec + toff + u0, lam, c, best, bx, by);
+    };
+    // two chunks per iteration where the registers allow: independent loads
+    // and max chains in flight
+    int c = c_lo;
+    if constexpr (R <= 8) {
+      for (; c + 1 < c_hi; c += 2) {
+        chunk(c);
+        chunk(c + 1);
       }
     }
-    // exact argmax: first action of the winning chunk that reproduces the max
-    // (the same two round-to-nearest operations as the packed evaluation)
-    const int xo = part * MWK + (m * W + b * R) * K + k0;
+    for (; c < c_hi; ++c) chunk(c);
+    // merge the parts of each cell: the larger value, on equal values the
+    // earlier chunk (the parts hold increasing action ranges)
+    for (int d = L; d < 32; d <<= 1) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = h ? by[j] : bx[j];
-        const float bj = h ? best[j].y : best[j].x;
-        const float lk = h ? lam.y : lam.x;
-        int arg = -1;
-        if (c >= 0) {
-          const bool second = c >= n0;
-          const int u0 = (second ? c - n0 : c) * R;
-          const int a0 = second ? g1.a0 : g0.a0;
-          const int src = second ? g1.src : g0.src;
-          const int toff = second ? n0 * R : 0;
-          const float* eb = sm.Es + ((size_t)src * rows + b * R + j + a0 + u0) * Ke + k0 + h;
-          const float2* ep = ec + toff + u0;
-          float v[R];
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float2 e = ep[i];
-            v[i] = fmaf(lk, e.x, e.y) + eb[(size_t)i * Ke];
-          }
-          int first = R - 1;
-#pragma unroll
-          for (int i = R - 1; i >= 0; --i)
-            if (v[i] == bj) first = i;
-          arg = a0 + u0 + first;
-        }
-        if (k0 + h < K) {
-          sm.Xs[xo + j * K + h] = bj;
-          Xi[xo + j * K + h] = arg;
-        }
+      for (int j = 0; j < R; ++j) {
+        merge_part(best[j].x, bx[j], d);
+        merge_part(best[j].y, by[j], d);
       }
     }
-  }
-  __syncthreads();
-
-  // 4. combine the action parts (in increasing action order) into part 0;
-  //    V'_t into the V tile
-  {
-    const int Wt = w.s1 - w.s0, Kv = v_stride(K);
-    for (int row = warp; row < M * Wt; row += nwarps) {
-      const int m = row / Wt, r = row - m * Wt;
-      for (int k = lane; k < K; k += 32) {
-        const int i = (m * W + r) * K + k;
-        float bv = sm.Xs[i];
-        int ba = Xi[i];
-        for (int qq = 1; qq < as.parts; ++qq) {
-          const float v = sm.Xs[qq * MWK + i];
-          if (v > bv) {
-            bv = v;
-            ba = Xi[qq * MWK + i];
+    // exact argmax of each entry, spread over the parts: the first action of
+    // the winning chunk that reproduces the max (the same two round-to-nearest
+    // operations as the packed evaluation); V'_t = max + c_{t+1} rho_t[k] - c_t
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (((2 * j + h) & (G - 1)) != part) continue;
+          const int row = b * R + j, k = k0 + h;
+          if (k >= K || row >= Wt) continue;
+          const int c = h ? by[j] : bx[j];
+          const float bj = h ? best[j].y : best[j].x;
+          const float lk = h ? lam.y : lam.x;
+          int arg = -1;
+          if (c >= 0) {
+            const bool second = c >= n0;
+            const int u0 = (second ? c - n0 : c) * R;
+            const int a0 = second ? g1.a0 : g0.a0;
+            const int src = second ? g1.src : g0.src;
+            const int toff = second ? n0 * R : 0;
+            const float* eb = sm.Es + ((size_t)src * rows + row + a0 + u0) * Ke + k;
+            const float2* ep = ec + toff + u0;
+            float v[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const float2 e = ep[i];
+              v[i] = fmaf(lk, e.x, e.y) + eb[(size_t)i * Ke];
+            }
+            int first = R - 1;
+#pragma unroll
+            for (int i = R - 1; i >= 0; --i)
+              if (v[i] == bj) first = i;
+            arg = a0 + u0 + first;
           }
+          sm.Vs[(m * W + row) * Kv + k] = bj + sm.delta[k];
+          Xi[(m * W + row) * K + k] = arg;
         }
-        bv += sm.delta[k];  // V'_t = max_a(r + EV') + c_{t+1} rho_t[k] - c_t
-        sm.Vs[(m * W + r) * Kv + k] = bv;
-        sm.Xs[i] = bv;
-        Xi[i] = ba;
       }
     }
   }
@@ -683,8 +703,8 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
                              const Smem& sm) {
   const int K = as.K, M = as.M, N = as.N, W = as.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int MWK = M * W * K;
-  const int* Xi = reinterpret_cast<const int*>(sm.Xs + (size_t)as.parts * MWK);
+  const int* Xi = reinterpret_cast<const int*>(sm.Xs);
+  const int Kv = v_stride(K);
   const size_t MNK = mnk(as);
   const int Wt = w.s1 - w.s0;
   const double lvl = sm.lvl[1];
@@ -698,9 +718,9 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
   for (int row = warp; row < M * Wt; row += nwarps) {
     const int m = row / Wt, r = row - m * Wt;
     const size_t ob = ((size_t)m * N + w.s0 + r) * K;
-    const int ib = (m * W + r) * K;
+    const int ib = (m * W + r) * K, vb = (m * W + r) * Kv;
     for (int k = lane; k < K; k += 32) {
-      const float bv = sm.Xs[ib + k];
+      const float bv = sm.Vs[vb + k];
       const int ba = Xi[ib + k];
       if (pol32) __stcs(pol32 + pbase + ob + k, ba);
       if (pol16) __stcs(pol16 + pbase + ob + k, (short)ba);
