@@ -40,7 +40,8 @@ struct Plan {
   std::vector<int> cta_items;
   int n_steps = 0;
   int n_flags = 0;
-  int sm_E = 0, sm_R = 0, sm_C = 0, sm_V = 0, sm_P = 0, sm_X = 0;
+  int sm_E = 0, sm_R = 0, sm_C = 0, sm_V = 0, sm_P = 0, sm_X = 0, sm_A = 0, sm_A2 = 0;
+  int tmem_cols = 0;
   AssetDev* d_assets = nullptr;
   WorkItem* d_items = nullptr;
   int* d_cta = nullptr;
@@ -173,7 +174,7 @@ struct AssetChoice {
 };
 
 size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R) {
-  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R).bytes;
+  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R, tc_shape(a.K)).bytes;
 }
 
 int n_chunks_min(const esdp_asset& a, int R) {
@@ -236,6 +237,8 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
   int flag_base = 0;
   // the launch's carve-up must hold every asset: take the largest region sizes
   long long need_E = 0, need_R = 0, need_C = 0, need_V = 0, need_P = 0, need_X = 0;
+  long long need_A = 0, need_foot = 0;  // tcgen05 operand part; footprint of its 128-row blocks
+  int tmem_cols = 0;
   for (size_t j = 0; j < ids.size(); ++j) {
     const esdp_asset& a = c->assets[ids[j]];
     const double work = (double)a.n_modes * a.N * a.K * a.A;
@@ -245,8 +248,17 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
                   "asset %d (K=%d, modes=%d, A=%d) does not fit a %d-thread tile in shared memory",
                   ids[j], a.K, a.n_modes, a.A, block);
     {
-      const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R);
-      const long long endX = (long long)(L.bytes / sizeof(float));
+      const bool tc = tc_shape(a.K);
+      const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R, tc);
+      const long long endX = L.X + ((long long)a.n_modes * ch[j].W * a.K + 31) / 32 * 32;
+      need_A = std::max<long long>(need_A, L.A2 - L.A);
+      if (tc) {
+        const long long mw64 = ((long long)a.n_modes * ch[j].W + 63) / 64 * 64;
+        need_foot = std::max<long long>(need_foot, mw64 / 8 * (a.K / 4) * kCmA);
+        int cols = 32;
+        while (cols < a.K) cols *= 2;
+        tmem_cols = std::max(tmem_cols, cols);
+      }
       need_E = std::max<long long>(need_E, L.Rt - L.E);
       need_R = std::max<long long>(need_R, L.C - L.Rt);
       need_C = std::max<long long>(need_C, L.V - L.C);
@@ -281,6 +293,7 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     d.evoff = c->d_evoff[ids[j]];
     d.c_start = nullptr;
     d.ptrans = c->d_ptrans[ids[j]];
+    d.tc = (d.ptrans != nullptr && tc_shape(a.K)) ? 1 : 0;  // the prepared layout follows K
     plan->max_rows = std::max(plan->max_rows, a.T * a.K);
     plan->adev.push_back(d);
     for (int tI = 0; tI < d.n_tiles; ++tI) {
@@ -294,13 +307,17 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     flag_base += d.n_tiles;
   }
   plan->n_flags = flag_base;
-  plan->sm_E = 0;
-  plan->sm_R = (int)need_E;
+  plan->sm_A = 0;
+  plan->sm_A2 = (int)need_A;
+  plan->sm_E = 2 * (int)need_A;
+  plan->sm_R = plan->sm_E + (int)need_E;
   plan->sm_C = plan->sm_R + (int)need_R;
   plan->sm_V = plan->sm_C + (int)need_C;
   plan->sm_P = plan->sm_V + (int)need_V;
   plan->sm_X = plan->sm_P + (int)need_P;
-  plan->shape.smem = (size_t)(plan->sm_X + need_X) * sizeof(float);
+  plan->tmem_cols = tmem_cols;
+  plan->shape.smem =
+      (size_t)std::max<long long>(plan->sm_X + need_X, plan->sm_A2 + need_foot) * sizeof(float);
   if (plan->shape.smem > kSmemLimit)
     return fail(c, ESDP_EINVAL, "shared memory plan of %zu bytes exceeds the limit",
                 plan->shape.smem);
@@ -407,6 +424,9 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
   sp.sm_V = p->sm_V;
   sp.sm_P = p->sm_P;
   sp.sm_X = p->sm_X;
+  sp.sm_A = p->sm_A;
+  sp.sm_A2 = p->sm_A2;
+  sp.tmem_cols = p->tmem_cols;
   CK(cudaMemsetAsync(p->d_flags, 0, std::max(1, p->n_flags) * sizeof(int), st), "reset flags");
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "reset status");
   CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
@@ -623,7 +643,8 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
     c->d_evoff.push_back(evoff);
     c->d_refh.push_back(refh);
     float* pt = nullptr;
-    if ((rc = dalloc(c, &pt, (size_t)a.T * a.K * p_stride(a.K)))) return rc;
+    const size_t per = tc_shape(a.K) ? 2 * (size_t)a.K * a.K : (size_t)a.K * p_stride(a.K);
+    if ((rc = dalloc(c, &pt, (size_t)a.T * per))) return rc;
     c->d_ptrans.push_back(pt);
   }
   if (!(flags & ESDP_DEVICE_PTRS)) {

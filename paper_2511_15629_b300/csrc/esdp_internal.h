@@ -47,8 +47,27 @@ struct AssetDev {
   double* off;          // [T+2]: off[t] = c_t (written by tile 0)
   double* evoff;        // [T][K]: EV_t - EV'_t = c_{t+1} rho_t[k] (written by tile 0)
   const double* c_start;  // c_{t_hi+1}, or nullptr for 0
-  float* ptrans;        // [T][K][p_stride(K)] transposed, padded P_t (prep kernel), or nullptr
+  float* ptrans;        // prepared P_t per stage (prep kernel), or nullptr: with tc == 0
+                        // [T][K][p_stride(K)] transposed and padded; with tc == 1
+                        // [T][2][K*K] tf32 hi and lo parts in the tensor-core operand layout
+  int tc;               // 1: EV contraction on tcgen05 (K a multiple of 16, ptrans prepared)
 };
+
+// The EV contraction on tcgen05 needs K a multiple of 16 (N of a 128-row MMA)
+// and the prepared operand copy of P.
+__host__ __device__ inline bool tc_shape(int K) { return K >= 16 && K <= 128 && (K & 15) == 0; }
+
+// Offset (floats) of element (r, k) of a [rows x KK] tcgen05 operand in the
+// K-major, unswizzled canonical layout: 8-row x 16-byte core matrices, the
+// KK/4 core matrices of one 8-row group `cm` floats apart (leading byte
+// offset 4 * cm), the 8-row groups KK/4 * cm floats apart (stride byte
+// offset).  cm = 32 packs them (the prepared B operand); cm = 36 leaves a
+// 16-byte gap that puts the 32 states of one row in 32 distinct banks (the A
+// operand, written row by row by the sweep).
+constexpr int kCmB = 32, kCmA = 36;
+__host__ __device__ inline int tc_offset(int r, int k, int KK, int cm) {
+  return (r >> 3) * (KK >> 2) * cm + (k >> 2) * cm + (r & 7) * 4 + (k & 3);
+}
 
 struct WorkItem {
   int asset, tile, s0, s1;  // rows [s0, s1) of the asset's SoC grid
@@ -71,6 +90,8 @@ struct SweepParams {
   double* item_c;            // [items] running level c of each work item
   // shared-memory carve-up (floats), see sweep_smem_layout
   int sm_E, sm_R, sm_C, sm_V, sm_P, sm_X;
+  int sm_A, sm_A2;           // tcgen05 A operand (V' split into tf32 hi and lo parts)
+  int tmem_cols;             // tensor-memory columns of the EV accumulator (0: none)
 };
 
 // Row strides of the V' tile and of the transposed transition matrix in
@@ -82,21 +103,32 @@ __host__ __device__ inline int p_stride(int K) { return ((K + 3) & ~3) + 8; }
 
 // Shared-memory carve-up of the sweep kernel (offsets in floats, every region
 // 128-byte aligned so that bulk copies and float4 accesses are aligned).
+// With the tensor-core EV (tc), the two A operand parts come first: each
+// holds the tile's M*W rows (rounded up to 8); a 64-row MMA reads past them
+// into the regions that follow (rows it computes but nobody stores), so the
+// carve-up extends at least whole 64-row blocks past the second part.
 struct SweepSmem {
-  int E, Rt, C, V, P, X;
+  int A, A2, E, Rt, C, V, P, X;
   size_t bytes;
 };
-inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R) {
+inline SweepSmem sweep_smem_layout(int M, int K, int W, int A, int R, bool tc) {
   auto al = [](long long x) { return (int)((x + 31) / 32 * 32); };
   const int rows = W + A + R, rs = (A + 2 * R) | 1;
+  const int mw8 = (M * W + 7) / 8 * 8, mw64 = (M * W + 63) / 64 * 64;
   SweepSmem s;
-  s.E = 0;
+  const long long apart = (long long)(mw8 / 8) * (K / 4) * kCmA;  // A part (floats)
+  s.A = 0;
+  s.A2 = s.A + (tc ? al(apart) : 0);
+  s.E = s.A2 + (tc ? al(apart) : 0);
   s.Rt = s.E + al((long long)M * rows * (K + (K & 1)));
   s.C = s.Rt;  // no payoff table: the payoffs are formed in registers
   s.V = s.C + al(2LL * M * rs);
   s.P = s.V + al((long long)M * W * v_stride(K));
-  s.X = s.P + al((long long)K * p_stride(K));
-  s.bytes = (size_t)(s.X + al((long long)M * W * K)) * sizeof(float);  // argmax indices
+  s.X = s.P + al(tc ? 2LL * K * K : (long long)K * p_stride(K));
+  long long end = s.X + al((long long)M * W * K);  // argmax indices
+  const long long foot = (long long)(mw64 / 8) * (K / 4) * kCmA;  // read by the 64-row blocks
+  if (tc && end < (long long)s.A2 + foot) end = (long long)s.A2 + foot;
+  s.bytes = (size_t)end * sizeof(float);
   return s;
 }
 

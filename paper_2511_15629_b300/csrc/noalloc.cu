@@ -121,7 +121,7 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
     if (2 * reach + 2 > block) continue;
     parts = pick_parts(KM * nb, block, chunks_min(a, R));
     if (parts < 1) continue;
-    L = sweep_smem_layout(M, K, W, a.A, R);
+    L = sweep_smem_layout(M, K, W, a.A, R, false);  // no prepared P: SIMT / mma.sync EV
     if (L.bytes <= kSmemLimit) break;
   }
   if (nb < 1) return msg(err, err_len, ESDP_EINVAL, "no launch shape fits shared memory");

@@ -179,6 +179,22 @@ __device__ __forceinline__ float* ev_ptr(const AssetDev& as, int t) {
   return as.ev_keep ? as.ev + (size_t)(t - 1) * mnk(as) : as.ev + (size_t)(t & 1) * mnk(as);
 }
 
+// Shared-memory regions and barriers of the sweep CTA.
+struct Smem {
+  float *Es, *Vs, *Ps, *Xs;
+  float2* EC;      // [M][rs] (grid energy e_a, -(cost_a + switch)), -inf padding
+  double* lvl;     // [2]: c_{t+1}, c_t
+  float* lam;      // [K] prices of the stage
+  float* delta;    // [K] level correction of the stage
+  float* ref;      // EV'_t[ref]
+  int* abort;
+  uint64_t* bar;   // EV tile bulk copies
+  uint64_t* barP;  // transposed P bulk copy
+  float *Ah, *Al;  // tcgen05 A operand: V' rows, tf32 hi and lo parts
+  uint64_t* barM;  // tcgen05 products of the EV contraction
+  uint32_t tmem;   // EV accumulator in tensor memory (lane 0, first column)
+};
+
 // Issue the asynchronous load of P_t transposed: Ps[k2*Kp4 + k] = trans[t][k][k2].
 __device__ __forceinline__ void prefetch_trans(const SweepParams& p, const AssetDev& as, int t,
                                                float* Ps) {
@@ -190,18 +206,19 @@ __device__ __forceinline__ void prefetch_trans(const SweepParams& p, const Asset
   }
 }
 
-// Start loading P_t^T into shared memory: one bulk copy of the prepared
-// transposed copy when there is one (completion on `bar`), else the cp.async
-// gather above.  Returns true if a bulk copy was issued.
+// Start loading P_t into shared memory: one bulk copy of the prepared copy
+// when there is one (transposed, or the tensor-core operand parts; completion
+// on `bar`), else the cp.async gather of P_t^T above.  Returns true if a bulk
+// copy was issued.
 __device__ __forceinline__ bool load_trans_async(const SweepParams& p, const AssetDev& as, int t,
                                                  float* Ps, uint64_t* bar) {
   if (as.ptrans) {
     if (threadIdx.x == 0) {
-      const int K = as.K, Kpt = p_stride(K);
-      const uint32_t bytes = (uint32_t)K * Kpt * 4u;
+      const int K = as.K;
+      const uint32_t per = as.tc ? 2u * K * K : (uint32_t)K * p_stride(K);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(bar, bytes);
-      bulk_load(Ps, as.ptrans + (size_t)(t - 1) * K * Kpt, bytes, bar);
+      mbar_expect_tx(bar, per * 4u);
+      bulk_load(Ps, as.ptrans + (size_t)(t - 1) * per, per * 4u, bar);
     }
     return true;
   }
@@ -272,6 +289,20 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = to_tf32(x);
   lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// V'_t entry (mode m, tile row r, state k) into the V tile and, on the
+// tensor-core path, into the two A operand parts (row m * Wt + r).
+__device__ __forceinline__ void put_v(float* Vs, float* Ah, float* Al, const AssetDev& as, int Wt,
+                                      int m, int r, int k, float v) {
+  Vs[(m * as.W + r) * v_stride(as.K) + k] = v;
+  if (as.tc) {
+    uint32_t hi, lo;
+    split_tf32(v, hi, lo);
+    const int o = tc_offset(m * Wt + r, k, as.K, kCmA);
+    Ah[o] = __uint_as_float(hi);
+    Al[o] = __uint_as_float(lo);
+  }
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -355,8 +386,128 @@ __device__ void expectation_mma(const AssetDev& as, const WorkItem& w, int te, c
   }
 }
 
-__device__ __forceinline__ void expectation(const AssetDev& as, const WorkItem& w, int te,
-                                            const float* Ps, const float* Vs, float* dst) {
+// ---- tcgen05 (5th-generation tensor cores, accumulator in tensor memory)
+
+// Shared-memory operand descriptor: start address, leading (K-adjacent core
+// matrices) and stride (8-row groups) byte offsets, descriptor version 1, no
+// swizzle.
+__device__ __forceinline__ uint64_t tc_desc(const float* p, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// D[128 x N] (+)= A . B^T, tf32 inputs, float32 accumulation in tensor memory
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive float32 columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tc_load16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// EV rows of the item on tcgen05: D[L][k] = sum_k2 A[L][k2] B[k][k2] with
+// A the tile's V' rows (row L = m * Wt + r) and B = P_te, both split into tf32
+// hi + lo parts; per k-step of 8 the products hi.lo, lo.hi and hi.hi
+// accumulate in float32 in tensor memory (float32-accurate).  Blocks of 64
+// rows (an M = 64 MMA keeps row i in lane 32 * (i / 16) + i % 16); thread 0
+// issues the MMAs and commits them to `barM`, the warps of each lane quarter
+// read their 16 rows back, 16 columns at a time, and store them.  A bounded
+// wait that expires leaves ESDP_ETIMEOUT in the status word (the next
+// neighbour wait then abandons the launch).
+__device__ void expectation_tc(const SweepParams& p, const AssetDev& as, const WorkItem& w, int te,
+                               const Smem& sm, uint32_t& parity_m) {
+  const int K = as.K, N = as.N;
+  const int Wt = w.s1 - w.s0, n_rows = as.M * Wt;
+  const int nblk = (n_rows + 63) >> 6;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int q = warp & 3, nq = (nwarps - q + 3) >> 2, wi = warp >> 2;
+  float* dst = ev_ptr(as, te);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // V' parts -> tensor core
+  for (int blk = 0; blk < nblk; ++blk) {
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (threadIdx.x == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) |
+                             ((uint32_t)(64 >> 4) << 24);
+      const uint32_t sbo_a = (uint32_t)(K >> 2) * kCmA * 4u, sbo_b = (uint32_t)(K >> 2) * kCmB * 4u;
+      const int o = blk * 8 * (K >> 2) * kCmA;  // 8 row groups per 64 rows
+      // k-step st covers core-matrix columns 2st, 2st + 1: the start address
+      // (16-byte units, low bits of the descriptor) advances by 2 cm floats
+      const uint64_t ah = tc_desc(sm.Ah + o, kCmA * 4u, sbo_a);
+      const uint64_t al = tc_desc(sm.Al + o, kCmA * 4u, sbo_a);
+      const uint64_t bh = tc_desc(sm.Ps, kCmB * 4u, sbo_b);
+      const uint64_t bl = tc_desc(sm.Ps + K * K, kCmB * 4u, sbo_b);
+      for (int st = 0; st < (K >> 3); ++st) {
+        const uint64_t da = (uint64_t)(st * kCmA / 2), db = (uint64_t)(st * kCmB / 2);
+        tc_mma(sm.tmem, ah + da, bl + db, idesc, st > 0);
+        tc_mma(sm.tmem, al + da, bh + db, idesc, 1u);
+        tc_mma(sm.tmem, ah + da, bh + db, idesc, 1u);
+      }
+      tc_commit(sm.barM);
+    }
+    const int row0 = blk * 64 + 16 * q;  // first row of this warp's lane quarter
+    if (row0 < n_rows && mbar_wait_bounded(sm.barM, parity_m, p)) {
+      tc_after_sync();
+      for (int c0 = 16 * wi; c0 < K; c0 += 16 * nq) {
+        float v[16];
+        tc_load16(sm.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+        const int L = row0 + lane;
+        if (lane < 16 && L < n_rows) {
+          const int m = L / Wt, r = L - m * Wt;
+          float4* d4 = reinterpret_cast<float4*>(dst + ((size_t)m * N + w.s0 + r) * K + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            __stcg(d4 + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+          if (m == 0 && c0 == 0 && w.s0 + r == as.ref_row) __stcg(as.ref_hist + te, v[0]);
+        }
+      }
+    }
+    parity_m ^= 1u;
+  }
+  tc_before_sync();
+}
+
+__device__ __forceinline__ void expectation(const SweepParams& p, const AssetDev& as,
+                                            const WorkItem& w, int te, const Smem& sm,
+                                            uint32_t& parity_m) {
+  if (as.tc) {
+    expectation_tc(p, as, w, te, sm, parity_m);
+    return;
+  }
+  const float* Ps = sm.Ps;
+  const float* Vs = sm.Vs;
+  float* dst = ev_ptr(as, te);
   if ((as.K & 7) == 0) {
     expectation_mma(as, w, te, Ps, Vs, dst);
     return;
@@ -392,16 +543,18 @@ __device__ bool wait_neighbours(const SweepParams& p, const AssetDev& as, const 
     const int* f = p.flags + as.flag_base + tile;
     if (ld_acquire(f) < need) {
       const unsigned long long t0 = now_ns();
-      while (true) {
+      for (unsigned it = 1;; ++it) {
         if (ld_acquire(f) >= need) break;
-        if (*(volatile int*)p.status != 0) {
-          *(volatile int*)s_abort = 1;
-          break;
-        }
-        if (now_ns() - t0 > p.timeout_ns) {
-          atomicCAS(p.status, 0, ESDP_ETIMEOUT);
-          *(volatile int*)s_abort = 1;
-          break;
+        if ((it & 15u) == 0) {  // the abort checks cost a round trip: not every poll
+          if (*(volatile int*)p.status != 0) {
+            *(volatile int*)s_abort = 1;
+            break;
+          }
+          if (now_ns() - t0 > p.timeout_ns) {
+            atomicCAS(p.status, 0, ESDP_ETIMEOUT);
+            *(volatile int*)s_abort = 1;
+            break;
+          }
         }
       }
     }
@@ -411,17 +564,6 @@ __device__ bool wait_neighbours(const SweepParams& p, const AssetDev& as, const 
   return *(volatile int*)s_abort == 0;
 }
 
-struct Smem {
-  float *Es, *Vs, *Ps, *Xs;
-  float2* EC;      // [M][rs] (grid energy e_a, -(cost_a + switch)), -inf padding
-  double* lvl;     // [2]: c_{t+1}, c_t
-  float* lam;      // [K] prices of the stage
-  float* delta;    // [K] level correction of the stage
-  float* ref;      // EV'_t[ref]
-  int* abort;
-  uint64_t* bar;   // EV tile bulk copies
-  uint64_t* barP;  // transposed P bulk copy
-};
 
 // Payoff columns of each mode: (e_a, -(cost_a + switch)), -inf padding to a
 // multiple of R per action segment; the payoff r = price*e_a - cost_a is
@@ -496,7 +638,7 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
                            int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p,
-                           bool p_pref) {
+                           uint32_t& parity_m, bool p_pref) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -649,51 +791,55 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
         merge_part(best[j].y, by[j], d);
       }
     }
-    // exact argmax of each entry, spread over the parts: the first action of
-    // the winning chunk that reproduces the max (the same two round-to-nearest
+    // exact argmax of each entry e = 2 j + h (row j, state k0 + h), spread
+    // over the parts: lane `part` takes e = part, part + G, ... in rounds, so
+    // every lane of a warp runs the same code.  The first action of the
+    // winning chunk that reproduces the max (the same two round-to-nearest
     // operations as the packed evaluation); V'_t = max + c_{t+1} rho_t[k] - c_t
     if (active) {
+      for (int e = part; e < 2 * R; e += G) {
+        const int j = e >> 1, h = e & 1;
+        float bj = 0.f;
+        int c = -1;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (((2 * j + h) & (G - 1)) != part) continue;
-          const int row = b * R + j, k = k0 + h;
-          if (k >= K || row >= Wt) continue;
-          const int c = h ? by[j] : bx[j];
-          const float bj = h ? best[j].y : best[j].x;
-          const float lk = h ? lam.y : lam.x;
-          int arg = -1;
-          if (c >= 0) {
-            const bool second = c >= n0;
-            const int u0 = (second ? c - n0 : c) * R;
-            const int a0 = second ? g1.a0 : g0.a0;
-            const int src = second ? g1.src : g0.src;
-            const int toff = second ? n0 * R : 0;
-            const float* eb = sm.Es + ((size_t)src * rows + row + a0 + u0) * Ke + k;
-            const float2* ep = ec + toff + u0;
-            float v[R];
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-              const float2 e = ep[i];
-              v[i] = fmaf(lk, e.x, e.y) + eb[(size_t)i * Ke];
-            }
-            int first = R - 1;
-#pragma unroll
-            for (int i = R - 1; i >= 0; --i)
-              if (v[i] == bj) first = i;
-            arg = a0 + u0 + first;
+        for (int jj = 0; jj < R; ++jj)
+          if (jj == j) {
+            bj = h ? best[jj].y : best[jj].x;
+            c = h ? by[jj] : bx[jj];
           }
-          sm.Vs[(m * W + row) * Kv + k] = bj + sm.delta[k];
-          Xi[(m * W + row) * K + k] = arg;
+        const int row = b * R + j, k = k0 + h;
+        if (k >= K || row >= Wt) continue;
+        const float lk = h ? lam.y : lam.x;
+        int arg = -1;
+        if (c >= 0) {
+          const bool second = c >= n0;
+          const int u0 = (second ? c - n0 : c) * R;
+          const int a0 = second ? g1.a0 : g0.a0;
+          const int src = second ? g1.src : g0.src;
+          const int toff = second ? n0 * R : 0;
+          const float* eb = sm.Es + ((size_t)src * rows + row + a0 + u0) * Ke + k;
+          const float2* ep = ec + toff + u0;
+          float v[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const float2 ei = ep[i];
+            v[i] = fmaf(lk, ei.x, ei.y) + eb[(size_t)i * Ke];
+          }
+          int first = R - 1;
+#pragma unroll
+          for (int i = R - 1; i >= 0; --i)
+            if (v[i] == bj) first = i;
+          arg = a0 + u0 + first;
         }
+        put_v(sm.Vs, sm.Ah, sm.Al, as, Wt, m, row, k, bj + sm.delta[k]);
+        Xi[(m * W + row) * K + k] = arg;
       }
     }
   }
   __syncthreads();
 
   // 5. EV'_{t-1} of the item's own rows
-  if (t > as.t_lo) expectation(as, w, t - 1, sm.Ps, sm.Vs, ev_ptr(as, t - 1));
+  if (t > as.t_lo) expectation(p, as, w, t - 1, sm, parity_m);
   return true;
 }
 
@@ -731,39 +877,12 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
   }
 }
 
+// The persistent sweep of one CTA: its work items for every stage.  Returns
+// early (uniformly over the CTA) when the launch is abandoned.
 template <int R>
-__global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p) {
-  extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
-  __shared__ int s_abort;
-  __shared__ double s_lvl[2];
-  __shared__ float s_lam[128];
-  __shared__ float s_delta[128];
-  __shared__ float s_ref;
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ __align__(8) uint64_t s_barP;
-  __shared__ __align__(16) AssetDev s_as;
-  Smem sm;
-  sm.Es = smem + p.sm_E;
-  sm.EC = reinterpret_cast<float2*>(smem + p.sm_C);
-  sm.Vs = smem + p.sm_V;
-  sm.Ps = smem + p.sm_P;
-  sm.Xs = smem + p.sm_X;
-  sm.lvl = s_lvl;
-  sm.lam = s_lam;
-  sm.delta = s_delta;
-  sm.ref = &s_ref;
-  sm.abort = &s_abort;
-  sm.bar = &s_bar;
-  sm.barP = &s_barP;
+__device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, AssetDev& s_as) {
   const int i0 = p.cta_items[blockIdx.x], i1 = p.cta_items[blockIdx.x + 1];
-  if (threadIdx.x == 0) {
-    s_abort = 0;
-    mbar_init(&s_bar);
-    mbar_init(&s_barP);
-  }
-  __syncthreads();
-  uint32_t parity = 0, parity_p = 0;
+  uint32_t parity = 0, parity_p = 0, parity_m = 0;
   // the work item's asset descriptor lives in shared memory: the loops that
   // store to global memory then need not reload its fields
   auto load_asset = [&](int a) {
@@ -790,8 +909,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
     const int Wt = w.s1 - w.s0, K = as.K;
     for (int i = threadIdx.x; i < as.M * Wt * K; i += blockDim.x) {
       const int k = i % K, r = (i / K) % Wt, m = i / (K * Wt);
-      sm.Vs[(m * as.W + r) * v_stride(K) + k] =
-          __ldcg(vst + ((size_t)m * as.N + w.s0 + r) * K + k);
+      put_v(sm.Vs, sm.Ah, sm.Al, as, Wt, m, r, k,
+            __ldcg(vst + ((size_t)m * as.N + w.s0 + r) * K + k));
     }
     if (threadIdx.x == 0) {
       const double c0 = as.c_start ? *as.c_start : 0.0;
@@ -800,12 +919,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
     }
     cp_async_wait_all();
     if (pb) {
-      if (threadIdx.x == 0 && !mbar_wait_bounded(sm.barP, parity_p, p)) s_abort = 1;
+      if (threadIdx.x == 0 && !mbar_wait_bounded(sm.barP, parity_p, p)) *sm.abort = 1;
       parity_p ^= 1u;
     }
     __syncthreads();
-    if (s_abort) return;
-    expectation(as, w, as.t_hi, sm.Ps, sm.Vs, ev_ptr(as, as.t_hi));
+    if (*(volatile int*)sm.abort) return;
+    expectation(p, as, w, as.t_hi, sm, parity_m);
     publish(p.flags + as.flag_base + w.tile, 1);
     __syncthreads();
   }
@@ -823,9 +942,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, pref)) return;
+      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref)) return;
       publish(p.flags + as.flag_base + w.tile, g + 2);
-      // start the next stage's P^T copy now when that stage is of the same
+      // start the next stage's P copy now when that stage is of the same
       // asset: its latency then overlaps the output stores and the wait
       {
         const int nit = it + 1 < i1 ? it + 1 : i0;
@@ -837,6 +956,66 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
       }
       item_outputs(p, as, w, as.t_hi - g, sm);
     }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ int s_abort;
+  __shared__ double s_lvl[2];
+  __shared__ float s_lam[128];
+  __shared__ float s_delta[128];
+  __shared__ float s_ref;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_barP;
+  __shared__ __align__(8) uint64_t s_barM;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(16) AssetDev s_as;
+  Smem sm;
+  sm.Es = smem + p.sm_E;
+  sm.EC = reinterpret_cast<float2*>(smem + p.sm_C);
+  sm.Vs = smem + p.sm_V;
+  sm.Ps = smem + p.sm_P;
+  sm.Xs = smem + p.sm_X;
+  sm.Ah = smem + p.sm_A;
+  sm.Al = smem + p.sm_A2;
+  sm.lvl = s_lvl;
+  sm.lam = s_lam;
+  sm.delta = s_delta;
+  sm.ref = &s_ref;
+  sm.abort = &s_abort;
+  sm.bar = &s_bar;
+  sm.barP = &s_barP;
+  sm.barM = &s_barM;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    mbar_init(&s_bar);
+    mbar_init(&s_barP);
+    mbar_init(&s_barM);
+  }
+  // tensor memory for the EV accumulator: allocated by warp 0 for the whole
+  // launch, freed on every way out
+  if (p.tmem_cols > 0 && threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  sm.tmem = p.tmem_cols > 0 ? s_tmem : 0u;
+  sweep_run<R>(p, sm, s_as);
+  tc_before_sync();
+  __syncthreads();
+  if (p.tmem_cols > 0 && threadIdx.x < 32) {
+    tc_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
   }
 }
 
@@ -855,7 +1034,19 @@ __global__ void rowsum_kernel(const AssetDev* assets, const float* trans) {
     for (int k2 = 0; k2 < K; ++k2) acc += (double)__ldg(P + r * K + k2);
     as.rho[r] = acc;
   }
-  if (as.ptrans) {
+  if (as.ptrans && as.tc) {
+    // [T][hi, lo][K*K]: B(k, k2) = P_t[k][k2] in the tcgen05 operand layout
+    const long long KK = (long long)K * K, n = (long long)as.T * KK;
+    for (long long i = first; i < n; i += stride) {
+      const long long t = i / KK;
+      const int kk = (int)(i - t * KK), k = kk / K, k2 = kk - k * K;
+      uint32_t hi, lo;
+      split_tf32(__ldg(P + i), hi, lo);
+      float* base = as.ptrans + t * 2 * KK;
+      base[tc_offset(k, k2, K, kCmB)] = __uint_as_float(hi);
+      base[KK + tc_offset(k, k2, K, kCmB)] = __uint_as_float(lo);
+    }
+  } else if (as.ptrans) {
     const long long n = rows * Kpt;  // [T][K][Kpt]
     for (long long i = first; i < n; i += stride) {
       const long long tk2 = i / Kpt;
