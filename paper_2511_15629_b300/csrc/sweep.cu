@@ -861,6 +861,35 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
   float* vk = as.v_keep ? as.v_keep + (size_t)(t - as.t_lo) * MNK : nullptr;
   float* cp = ck ? as.ckpt + (size_t)((t - 1) / as.ckpt_every - 1) * MNK : nullptr;
   float* v1 = (t == 1 && p.v1) ? p.v1 + as.off_v1 : nullptr;
+  const bool vec = (K & 3) == 0 && ((reinterpret_cast<uintptr_t>(as.policy) |
+                                      reinterpret_cast<uintptr_t>(as.v_keep) |
+                                      reinterpret_cast<uintptr_t>(as.ckpt)) & 15) == 0;
+  if (vec) {
+    // four states per thread: 16-byte shared reads and global stores (the
+    // per-stage and per-row offsets are multiples of 4 elements; V_1 sits at
+    // an arbitrary offset of the caller's array and is written per element)
+    const int K4 = K >> 2, n = M * Wt * K4;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int row = i / K4, k = (i - row * K4) << 2;
+      const int m = row / Wt, r = row - m * Wt;
+      const size_t o = ((size_t)m * N + w.s0 + r) * K + k;
+      const float4 bv = *reinterpret_cast<const float4*>(sm.Vs + (m * W + r) * Kv + k);
+      const int4 ba = *reinterpret_cast<const int4*>(Xi + (m * W + r) * K + k);
+      if (pol32) __stcs(reinterpret_cast<int4*>(pol32 + pbase + o), ba);
+      if (pol16)
+        __stcs(reinterpret_cast<short4*>(pol16 + pbase + o),
+               make_short4((short)ba.x, (short)ba.y, (short)ba.z, (short)ba.w));
+      if (vk) __stcg(reinterpret_cast<float4*>(vk + o), bv);
+      if (cp) __stcg(reinterpret_cast<float4*>(cp + o), bv);
+      if (v1) {
+        v1[o] = (float)((double)bv.x + lvl);
+        v1[o + 1] = (float)((double)bv.y + lvl);
+        v1[o + 2] = (float)((double)bv.z + lvl);
+        v1[o + 3] = (float)((double)bv.w + lvl);
+      }
+    }
+    return;
+  }
   for (int row = warp; row < M * Wt; row += nwarps) {
     const int m = row / Wt, r = row - m * Wt;
     const size_t ob = ((size_t)m * N + w.s0 + r) * K;
