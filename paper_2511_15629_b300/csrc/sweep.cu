@@ -634,11 +634,30 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
   }
 }
 
+// Per-thread scalars of stage t of work item `it`: threads below K hold the
+// price and the row sum of P_{t-1} of their state, thread 0 the item's running
+// level c_{t+1}.
+struct StageScalars {
+  float lam = 0.f;
+  double rho = 0.0, c = 0.0;
+  bool valid = false;
+};
+
+__device__ __forceinline__ void stage_scalars(const SweepParams& p, const AssetDev& as, int t,
+                                              int it, float& lam, double& rho, double& c) {
+  const int K = as.K, tid = threadIdx.x;
+  if (tid < K) {
+    lam = __ldg(p.price + as.off_price + (size_t)(t - 1) * K + tid);
+    rho = __ldg(as.rho + (size_t)(t - 1) * K + tid);
+  }
+  if (tid == 0) c = *(volatile double*)(p.item_c + it);
+}
+
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
                            int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p,
-                           uint32_t& parity_m, bool p_pref) {
+                           uint32_t& parity_m, bool p_pref, const StageScalars& pre) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -646,17 +665,13 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   const bool tma = (K & 3) == 0;
   const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
 
-  // 0. prefetch the inputs of the stage
-  // (the bulk copy of P_{t-1}^T may already be in flight: issued right after
-  // the previous stage's release)
+  // 0. inputs of the stage: the bulk copy of P_{t-1} and the per-thread
+  // scalars (price, row sum, running level) may already be in flight, issued
+  // right after the previous stage's release
   const bool p_bulk = p_pref || (t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP));
-  float lam_k = 0.f;
-  double rho_k = 0.0, c_next = 0.0;
-  if (tid < K) {
-    lam_k = __ldg(p.price + as.off_price + (size_t)(t - 1) * K + tid);
-    rho_k = __ldg(as.rho + (size_t)(t - 1) * K + tid);
-  }
-  if (tid == 0) c_next = p.item_c[it];
+  float lam_k = pre.lam;
+  double rho_k = pre.rho, c_next = pre.c;
+  if (!pre.valid) stage_scalars(p, as, t, it, lam_k, rho_k, c_next);
 
   // 1. neighbours
   if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
@@ -797,6 +812,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     // winning chunk that reproduces the max (the same two round-to-nearest
     // operations as the packed evaluation); V'_t = max + c_{t+1} rho_t[k] - c_t
     if (active) {
+#pragma unroll 2
       for (int e = part; e < 2 * R; e += G) {
         const int j = e >> 1, h = e & 1;
         float bj = 0.f;
@@ -924,6 +940,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
   };
   int cur_asset = -1, cols_asset = -1;
   bool pref = false;
+  StageScalars pre;
 
   // prologue: EV'_{t_hi} = P_{t_hi} V'_{t_hi+1} for the item's rows
   for (int it = i0; it < i1; ++it) {
@@ -958,9 +975,13 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
     __syncthreads();
   }
 
+  // the next work item's descriptor is read right after each release (off
+  // the stage's critical path) and carried over
+  int nx_idx = -1;
+  WorkItem nx{};
   for (int g = 0; g < p.n_steps; ++g) {
     for (int it = i0; it < i1; ++it) {
-      const WorkItem w = p.items[it];
+      const WorkItem w = it == nx_idx ? nx : p.items[it];
       if (w.asset != cur_asset) {
         load_asset(w.asset);
         cur_asset = w.asset;
@@ -971,17 +992,21 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref)) return;
+      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre)) return;
       publish(p.flags + as.flag_base + w.tile, g + 2);
-      // start the next stage's P copy now when that stage is of the same
-      // asset: its latency then overlaps the output stores and the wait
+      // start the next stage's loads now when that stage is of the same
+      // asset: their latency then overlaps the output stores and the wait
       {
         const int nit = it + 1 < i1 ? it + 1 : i0;
         const int ng = it + 1 < i1 ? g : g + 1;
         const int nt = as.t_hi - ng;
-        pref = as.ptrans != nullptr && ng < p.n_steps && p.items[nit].asset == w.asset &&
-               ng <= as.t_hi - as.t_lo && nt > as.t_lo;
+        nx = nit == it ? w : p.items[nit];
+        nx_idx = nit;
+        const bool next = ng < p.n_steps && nx.asset == w.asset && ng <= as.t_hi - as.t_lo;
+        pref = next && as.ptrans != nullptr && nt > as.t_lo;
         if (pref) load_trans_async(p, as, nt - 1, sm.Ps, sm.barP);
+        pre.valid = next;
+        if (next) stage_scalars(p, as, nt, nit, pre.lam, pre.rho, pre.c);
       }
       item_outputs(p, as, w, as.t_hi - g, sm);
     }
