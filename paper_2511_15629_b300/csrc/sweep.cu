@@ -653,11 +653,21 @@ __device__ __forceinline__ void stage_scalars(const SweepParams& p, const AssetD
   if (tid == 0) c = *(volatile double*)(p.item_c + it);
 }
 
+__device__ void item_outputs(const SweepParams& p, const AssetDev& as, const WorkItem& w, int t,
+                             const Smem& sm, int first);
+
+// A stage whose outputs are still to be written (it < 0: none).
+struct Deferred {
+  int it = -1, t = 0;
+  WorkItem w{};
+};
+
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
                            int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p,
-                           uint32_t& parity_m, bool p_pref, const StageScalars& pre) {
+                           uint32_t& parity_m, bool p_pref, const StageScalars& pre,
+                           const Deferred& def) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -673,7 +683,13 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   double rho_k = pre.rho, c_next = pre.c;
   if (!pre.valid) stage_scalars(p, as, t, it, lam_k, rho_k, c_next);
 
-  // 1. neighbours
+  // 1. neighbours; meanwhile the warps that do not poll write the previous
+  //    stage's outputs (its V' tile and indices are still in place)
+  if (def.it >= 0) {
+    const int n_wait = min(as.n_tiles - 1, w.tile + as.wait_hi) - max(0, w.tile + as.wait_lo) + 2;
+    const int first = (n_wait + 31) & ~31;
+    item_outputs(p, as, def.w, def.t, sm, first < (int)blockDim.x ? first : 0);
+  }
   if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
 
   // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
@@ -859,12 +875,17 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   return true;
 }
 
-// After the publish: the streaming outputs of the stage (policy, values kept
-// for the adjoint, checkpoints, V_1), read from the combined part-0 results.
+// The streaming outputs of a stage (policy, values kept for the adjoint,
+// checkpoints, V_1), read from the V' tile and the argmax indices: written
+// while the next stage of the CTA waits for its neighbours (or right after the
+// release when no such stage follows).
+// Run by the threads from `first` (a multiple of 32) on.
 __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const WorkItem& w, int t,
-                             const Smem& sm) {
+                             const Smem& sm, int first) {
   const int K = as.K, M = as.M, N = as.N, W = as.W;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x - first) >> 5,
+            nwarps = (blockDim.x - first) >> 5;
+  if ((int)threadIdx.x < first) return;
   const int* Xi = reinterpret_cast<const int*>(sm.Xs);
   const int Kv = v_stride(K);
   const size_t MNK = mnk(as);
@@ -885,7 +906,7 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
     // per-stage and per-row offsets are multiples of 4 elements; V_1 sits at
     // an arbitrary offset of the caller's array and is written per element)
     const int K4 = K >> 2, n = M * Wt * K4;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x - first; i < n; i += blockDim.x - first) {
       const int row = i / K4, k = (i - row * K4) << 2;
       const int m = row / Wt, r = row - m * Wt;
       const size_t o = ((size_t)m * N + w.s0 + r) * K + k;
@@ -979,9 +1000,14 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
   // the stage's critical path) and carried over
   int nx_idx = -1;
   WorkItem nx{};
+  Deferred def;
   for (int g = 0; g < p.n_steps; ++g) {
     for (int it = i0; it < i1; ++it) {
       const WorkItem w = it == nx_idx ? nx : p.items[it];
+      if (w.asset != cur_asset && def.it >= 0) {
+        item_outputs(p, s_as, def.w, def.t, sm, 0);  // before the descriptor changes
+        def.it = -1;
+      }
       if (w.asset != cur_asset) {
         load_asset(w.asset);
         cur_asset = w.asset;
@@ -992,7 +1018,8 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre)) return;
+      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre, def)) return;
+      def.it = -1;
       publish(p.flags + as.flag_base + w.tile, g + 2);
       // start the next stage's loads now when that stage is of the same
       // asset: their latency then overlaps the output stores and the wait
@@ -1007,10 +1034,19 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         if (pref) load_trans_async(p, as, nt - 1, sm.Ps, sm.barP);
         pre.valid = next;
         if (next) stage_scalars(p, as, nt, nit, pre.lam, pre.rho, pre.c);
+        // this stage's outputs: during the next stage's wait when one follows
+        // on this asset, else now
+        if (next) {
+          def.it = it;
+          def.t = as.t_hi - g;
+          def.w = w;
+        } else {
+          item_outputs(p, as, w, as.t_hi - g, sm, 0);
+        }
       }
-      item_outputs(p, as, w, as.t_hi - g, sm);
     }
   }
+  if (def.it >= 0) item_outputs(p, s_as, def.w, def.t, sm, 0);
 }
 
 template <int R>
