@@ -129,11 +129,19 @@ int esdp_objective(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, vo
  * policy (envelope theorem on eq. 5-6; exact away from ties).  With
  * ckpt_every = C > 0 the policies are recomputed segment by segment from the
  * V checkpoints; otherwise the whole horizon is recomputed once.  Uses the
- * inputs of the last esdp_solve.  mu0 [K] in; J [1] (double), d_price [T*K],
- * d_trans [T*K*K] (float), d_eta [2] (double: dJ/deta_c, dJ/deta_d) out;
- * any output may be NULL. */
+ * inputs of the last esdp_solve.  In: mu0 [K].  Out (any may be NULL):
+ *   J          [1]         double
+ *   d_price    [T*K]       float   dJ/dprice[t][k]
+ *   d_trans    [T*K*K]     float   dJ/dtrans[t][k][k2]
+ *   d_eta      [2]         double  dJ/deta_c, dJ/deta_d
+ *   d_cost     [A]         float   dJ/dcost[a] (the per-action cost array)
+ *   d_switch   [1]         double  dJ/dswitch_cost (0 with one mode)
+ *   d_terminal [n_modes*N*K] float dJ/dterminal = the occupancy after stage T
+ *   d_mu0      [K]         float   dJ/dmu0[k] = V_1[0][s0][k]
+ * Device or host pointers as the context's flags say; blocks until done. */
 int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* d_price,
-              float* d_trans, double* d_eta, void* stream);
+              float* d_trans, double* d_eta, float* d_cost, double* d_switch, float* d_terminal,
+              float* d_mu0, void* stream);
 
 /* Re-time the candidate tile shapes / actions-per-warp on the device and
  * keep the fastest (results are cached per shape class for the process). */

@@ -195,13 +195,17 @@ int orc_hull(int N, const double* y, int stride, int32_t* idx) {
  *   dtrans[t][k][k2]  = sum_{m,s} post_t[m][s][k] * V_{t+1}[m][s][k2]
  *   deta_c            = sum rho_t * price[t][k] * de/deta_c (charge: d*delta/eta_c^2)
  *   deta_d            = sum rho_t * price[t][k] * de/deta_d (discharge: -d*delta)
+ *   dcost[a]          = -sum_t sum rho_t * [pi_t = a]       (cost[a] enters every payoff of a)
+ *   dswitch           = -sum rho_t * [m = 1, d < 0]          (two modes)
+ *   dterminal[m][s][k] = rho_{T+1}[m][s][k]                 (J holds E[V_{T+1}] linearly)
  *   exp_reward[t]     = sum rho_t * r  (so J = sum_t exp_reward + E[V_{T+1}])
  *   V_all: (T+1) blocks as produced by orc_solve (block t holds V_{t+1}).
  */
 int orc_occupancy(const orc_problem* p, const double* price, const double* trans, const double* cost,
                   const int32_t* policy, const double* V_all, int s0, const double* mu0, double* J,
                   double* J_occ, double* dprice, double* dtrans, double* deta_c, double* deta_d,
-                  double* exp_reward, double* mass) {
+                  double* exp_reward, double* mass, double* dcost, double* dswitch,
+                  double* dterminal) {
   if (check(p)) return -1;
   int M = p->n_modes, N = p->N, K = p->K, T = p->T;
   size_t L = (size_t)M * N * K;
@@ -218,7 +222,8 @@ int orc_occupancy(const orc_problem* p, const double* price, const double* trans
     j += mu0[k] * V_all[IDX3(0, s0, k, N, K)];
   }
   *J = j;
-  double jo = 0.0, dc = 0.0, dd = 0.0;
+  double jo = 0.0, dc = 0.0, dd = 0.0, dsw = 0.0;
+  for (int a = 0; a < p->A; ++a) dcost[a] = 0.0;
   for (int t = 1; t <= T; ++t) {
     const int32_t* pol = policy + (size_t)(t - 1) * L;
     const double* Vn = V_all + (size_t)t * L;
@@ -239,6 +244,9 @@ int orc_occupancy(const orc_problem* p, const double* price, const double* trans
           dprice[(size_t)(t - 1) * K + k] += r0 * action_energy(p, a);
           if (d > 0) dc += r0 * lam * ((double)d * delta / (p->eta_c * p->eta_c));
           if (d < 0) dd += r0 * lam * (-(double)d * delta);
+          /* the payoff carries -cost[a] and, from mode 1 into a discharge, -switch_cost */
+          dcost[a] -= r0;
+          if (M == 2 && m == 1 && d < 0) dsw -= r0;
           er += r0 * payoff(p, lam, cost, m, a);
           ms += r0;
         }
@@ -262,9 +270,12 @@ int orc_occupancy(const orc_problem* p, const double* price, const double* trans
   }
   const double* VT1 = V_all + (size_t)T * L;
   for (size_t i = 0; i < L; ++i) jo += rho[i] * VT1[i];
+  /* J depends on the terminal value through E[V_{T+1}]: the final occupancy */
+  for (size_t i = 0; i < L; ++i) dterminal[i] = rho[i];
   *J_occ = jo;
   *deta_c = dc;
   *deta_d = dd;
+  *dswitch = dsw;
   free(rho); free(post);
   return 0;
 }

@@ -68,7 +68,7 @@ def _load():
                                    ctypes.c_int]
         _lib.orc_hull.argtypes = [ctypes.c_int, dp, ctypes.c_int, ip]
         _lib.orc_occupancy.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, ip, dp, ctypes.c_int,
-                                       dp, dp, dp, dp, dp, dp, dp, dp, dp]
+                                       dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
     return _lib
 
 
@@ -188,13 +188,20 @@ def occupancy(inst, policy: np.ndarray, V: np.ndarray, *, price=None, trans=None
     dd = np.zeros(1)
     er = np.zeros(T)
     mass = np.zeros(T)
+    dcost = np.zeros(p.A)
+    dsw = np.zeros(1)
+    dterm = np.zeros((p.n_modes, p.N, K))
     rc = lib.orc_occupancy(ctypes.byref(p), _dp(price), _dp(trans), _dp(cost), _ip(policy),
                            _dp(V), int(inst.s0), _dp(mu0), _dp(J), _dp(J_occ), _dp(dprice),
-                           _dp(dtrans), _dp(dc), _dp(dd), _dp(er), _dp(mass))
+                           _dp(dtrans), _dp(dc), _dp(dd), _dp(er), _dp(mass), _dp(dcost),
+                           _dp(dsw), _dp(dterm))
     if rc != 0:
         raise ValueError(f"orc_occupancy failed ({rc})")
+    # J = sum_k mu0[k] V_1[0][s0][k] is linear in mu0
+    d_mu0 = np.asarray(V[0, 0, inst.s0, :], dtype=np.float64).copy()
     return {"J": float(J[0]), "J_occ": float(J_occ[0]), "d_price": dprice, "d_trans": dtrans,
-            "d_eta_c": float(dc[0]), "d_eta_d": float(dd[0]), "exp_reward": er, "mass": mass}
+            "d_eta_c": float(dc[0]), "d_eta_d": float(dd[0]), "exp_reward": er, "mass": mass,
+            "d_cost": dcost, "d_switch": float(dsw[0]), "d_terminal": dterm, "d_mu0": d_mu0}
 
 
 # --------------------------------------------------------------------------

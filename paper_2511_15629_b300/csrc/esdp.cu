@@ -877,7 +877,8 @@ __global__ void to_float_kernel(const double* src, float* dst, long long n) {
 }  // namespace
 
 extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J,
-                         float* d_price, float* d_trans, double* d_eta, void* stream) {
+                         float* d_price, float* d_trans, double* d_eta, float* d_cost,
+                         double* d_switch, float* d_terminal, float* d_mu0, void* stream) {
   if (!c || !mu0) return ESDP_EINVAL;
   if (asset < 0 || asset >= (int32_t)c->assets.size())
     return fail(c, ESDP_EINVAL, "asset index %d out of range", asset);
@@ -911,13 +912,15 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     cudaStreamSynchronize(st);
     for (void* p : scratch) cudaFree(p);
   };
-  void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr;
+  void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
+      *dcost64, *dco;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
   if (!alloc(&seg_pol, L * C * pb) || !alloc(&seg_v, L * (C + 1) * 4) ||
       !alloc(&seg_post, L * C * 4) || !alloc(&rho, L * 4) || !alloc(&ev2, 2 * L * 4) ||
-      !alloc(&dprice64, (size_t)T * K * 8) || !alloc(&acc, 4 * 8) || !alloc(&bar, 4) ||
+      !alloc(&dprice64, (size_t)T * K * 8) || !alloc(&acc, 8 * 8) || !alloc(&bar, 4) ||
       !alloc(&d_mu, K * 4) || !alloc(&dJ, 8) || !alloc(&dtr, (size_t)T * K * K * 4) ||
-      !alloc(&dpr, (size_t)T * K * 4)) {
+      !alloc(&dpr, (size_t)T * K * 4) || !alloc(&dcost64, (size_t)a.A * 8) ||
+      !alloc(&dco, (size_t)a.A * 4)) {
     release();
     return fail(c, ESDP_ENOMEM, "gradient scratch allocation failed");
   }
@@ -931,7 +934,8 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     return cfail(e, "mu0 copy");
   cudaMemsetAsync(rho, 0, L * 4, st);
   cudaMemsetAsync(dprice64, 0, (size_t)T * K * 8, st);
-  cudaMemsetAsync(acc, 0, 32, st);
+  cudaMemsetAsync(acc, 0, 64, st);
+  cudaMemsetAsync(dcost64, 0, (size_t)a.A * 8, st);
   init_rho_kernel<<<1, 128, 0, st>>>((float*)rho, (const float*)d_mu, K, a.s0);
   objective_kernel<<<1, 32, 0, st>>>(c->last_v1 + c->off_v1[asset], (const float*)d_mu, K, a.s0,
                                       (double*)dJ);
@@ -990,6 +994,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.post = (float*)seg_post;
     op.d_price = (double*)dprice64;
     op.acc = (double*)acc;
+    op.d_cost = (double*)dcost64;
     op.bar = (int*)bar;
     op.status = c->d_status;
     op.timeout_ns = c->timeout_ns;
@@ -1013,6 +1018,16 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   if (d_price) cudaMemcpyAsync(d_price, dpr, nP * 4, k, st);
   if (d_trans) cudaMemcpyAsync(d_trans, dtr, (size_t)T * K * K * 4, k, st);
   if (d_eta) cudaMemcpyAsync(d_eta, acc, 16, k, st);
+  if (d_cost) {
+    to_float_kernel<<<(unsigned)((a.A + 255) / 256), 256, 0, st>>>((const double*)dcost64,
+                                                                    (float*)dco, a.A);
+    cudaMemcpyAsync(d_cost, dco, (size_t)a.A * 4, k, st);
+  }
+  if (d_switch) cudaMemcpyAsync(d_switch, (const double*)acc + 4, 8, k, st);
+  // after the last segment the occupancy buffer holds rho_{T+1}
+  if (d_terminal) cudaMemcpyAsync(d_terminal, rho, L * 4, k, st);
+  if (d_mu0)
+    cudaMemcpyAsync(d_mu0, c->last_v1 + c->off_v1[asset] + (size_t)a.s0 * K, (size_t)K * 4, k, st);
   int status = 0;
   cudaMemcpyAsync(&status, c->d_status, 4, cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);

@@ -191,7 +191,8 @@ struct OccParams {
   float* rho;             // [M][N][K], holds rho_{t_lo} on entry, rho_{t_hi+1} on exit
   float* post;            // [C][M][N][K], zero on entry
   double* d_price;        // [T][K] (accumulated)
-  double* acc;            // [4]: d_eta_c, d_eta_d, J_occ (expected reward), mass
+  double* acc;            // [5]: d_eta_c, d_eta_d, J_occ (expected reward), mass, d_switch
+  double* d_cost;         // [A] (accumulated)
   int* bar;               // grid barrier counter (zero on entry)
   int* status;
   unsigned long long timeout_ns;

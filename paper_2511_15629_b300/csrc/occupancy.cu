@@ -12,6 +12,9 @@
 //   dJ/dP_t[k][k2]         = sum_{m,s} post_t[m][s][k] V_{t+1}[m][s][k2]
 //   dJ/deta_c              = sum rho_t price[t][k] d delta / eta_c^2   (d > 0)
 //   dJ/deta_d              = sum rho_t price[t][k] (-d) delta           (d < 0)
+//   dJ/dcost[a]            = -sum_t sum rho_t [a_t = a]
+//   dJ/dswitch             = -sum rho_t [m = 1, d < 0]                  (two modes)
+//   dJ/dterminal           = rho_{T+1}, dJ/dmu0[k] = V_1[0][s0][k]  (taken by the host)
 // occ_kernel runs the forward pass over a segment of stages in one
 // cooperative launch (one bounded grid barrier per stage, between the scatter
 // and the contraction); dtrans_kernel then forms dJ/dP for the segment from
@@ -68,8 +71,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   extern __shared__ double osm[];
-  double* sk = osm;                                      // [K] dprice partials, then [4]
-  float* Ps = reinterpret_cast<float*>(osm + p.K + 4);   // [K][K]
+  double* sk = osm;                                          // [K] dprice partials, then [5]
+  double* sc = osm + p.K + 5;                                // [A] cost partials (segment)
+  float* Ps = reinterpret_cast<float*>(osm + p.K + 5 + p.A);  // [K][K]
   __shared__ int s_abort;
   const int K = p.K, N = p.N, M = p.M, MN = M * N;
   const size_t MNK = (size_t)MN * K;
@@ -77,15 +81,16 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   const int r0 = blockIdx.x * p.grid_rows;
   const int r1 = min(MN, r0 + p.grid_rows);
   if (tid == 0) s_abort = 0;
+  for (int a = tid; a < p.A; a += nth) sc[a] = 0.0;
   __syncthreads();
   int epoch = 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
-    for (int i = tid; i < K + 4; i += nth) sk[i] = 0.0;
+    for (int i = tid; i < K + 5; i += nth) sk[i] = 0.0;
     __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
     const float* price_t = p.price + (size_t)(t - 1) * K;
-    double dc = 0.0, dd = 0.0, jr = 0.0, ms = 0.0;
+    double dc = 0.0, dd = 0.0, jr = 0.0, ms = 0.0, dsw = 0.0;
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const float rho = p.rho[i];
       if (rho == 0.f) continue;
@@ -107,7 +112,11 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       if (d > 0) dc += (double)rho * lam * ((double)d * p.delta / (p.eta_c * p.eta_c));
       if (d < 0) dd += (double)rho * lam * (-(double)d * p.delta);
       double r = lam * e - (double)p.cost[a];
-      if (M == 2 && m == 1 && d < 0) r -= (double)p.sw;
+      atomicAdd(&sc[a], -(double)rho);
+      if (M == 2 && m == 1 && d < 0) {
+        r -= (double)p.sw;
+        dsw -= (double)rho;
+      }
       jr += (double)rho * r;
       ms += (double)rho;
     }
@@ -115,16 +124,21 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     dd = warp_sum(dd);
     jr = warp_sum(jr);
     ms = warp_sum(ms);
+    dsw = warp_sum(dsw);
     if ((tid & 31) == 0) {
       atomicAdd(&sk[K + 0], dc);
       atomicAdd(&sk[K + 1], dd);
       atomicAdd(&sk[K + 2], jr);
       atomicAdd(&sk[K + 3], ms);
+      atomicAdd(&sk[K + 4], dsw);
     }
     __syncthreads();
     for (int k = tid; k < K; k += nth)
       if (sk[k] != 0.0) atomicAdd(&p.d_price[(size_t)(t - 1) * K + k], sk[k]);
-    if (tid < 4 && sk[K + tid] != 0.0) atomicAdd(&p.acc[tid], sk[K + tid]);
+    if (tid < 5 && sk[K + tid] != 0.0) atomicAdd(&p.acc[tid], sk[K + tid]);
+    if (t == p.t_hi)  // the segment's cost partials, once
+      for (int a = tid; a < p.A; a += nth)
+        if (sc[a] != 0.0) atomicAdd(&p.d_cost[a], sc[a]);
     ++epoch;
     if (!grid_barrier(p.bar, epoch * (int)gridDim.x, p.status, p.timeout_ns, &s_abort)) return;
     // contraction of the post-decision occupancy with P_t (own rows)
@@ -179,7 +193,8 @@ __global__ void dtrans_kernel(const DTransParams p) {
 }  // namespace
 
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream) {
-  const size_t smem = (size_t)(p.K + 4) * sizeof(double) + (size_t)p.K * p.K * sizeof(float);
+  const size_t smem =
+      (size_t)(p.K + 5 + p.A) * sizeof(double) + (size_t)p.K * p.K * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(occ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -74,7 +74,7 @@ def load_library():
     lib.esdp_expected_value.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_bid_curves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
     lib.esdp_objective.argtypes = [vp, i32, vp, vp, vp]
-    lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
     lib.esdp_status.argtypes = [vp, vp]
     lib.esdp_launch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 6
@@ -252,7 +252,12 @@ class Solver:
                                              ptr(J, np.float64), _stream(stream)))
         return J
 
-    def grad(self, asset: int, mu0, J=None, d_price=None, d_trans=None, d_eta=None, stream=None):
+    def grad(self, asset: int, mu0, J=None, d_price=None, d_trans=None, d_eta=None,
+             d_cost=None, d_switch=None, d_terminal=None, d_mu0=None, stream=None, extra=False):
+        """Sensitivities of J (esdp_grad).  Host mode allocates the outputs it
+        is not given: (J, d_price, d_trans, d_eta), plus (d_cost, d_switch,
+        d_terminal, d_mu0) with extra=True.  Device mode writes the tensors it
+        is given (None: not computed)."""
         inst = self.instances[asset]
         if not self.device:
             mu0 = np.ascontiguousarray(mu0, dtype=np.float32)
@@ -261,13 +266,23 @@ class Solver:
             d_trans = (np.zeros((inst.T, inst.K, inst.K), np.float32) if d_trans is None
                        else d_trans)
             d_eta = np.zeros(2, np.float64) if d_eta is None else d_eta
+            if extra:
+                d_cost = np.zeros(inst.A, np.float32) if d_cost is None else d_cost
+                d_switch = np.zeros(1, np.float64) if d_switch is None else d_switch
+                d_terminal = (np.zeros((inst.n_modes, inst.N, inst.K), np.float32)
+                              if d_terminal is None else d_terminal)
+                d_mu0 = np.zeros(inst.K, np.float32) if d_mu0 is None else d_mu0
             ptr = lambda a, dt: _host_ptr(a, dt)
         else:
             ptr = lambda a, dt: _dev_ptr(a)
         self._check(self._lib.esdp_grad(self._ctx, asset, ptr(mu0, np.float32),
                                         ptr(J, np.float64), ptr(d_price, np.float32),
                                         ptr(d_trans, np.float32), ptr(d_eta, np.float64),
+                                        ptr(d_cost, np.float32), ptr(d_switch, np.float64),
+                                        ptr(d_terminal, np.float32), ptr(d_mu0, np.float32),
                                         _stream(stream)))
+        if extra:
+            return J, d_price, d_trans, d_eta, d_cost, d_switch, d_terminal, d_mu0
         return J, d_price, d_trans, d_eta
 
     def autotune(self, stream=None):

@@ -73,7 +73,8 @@ def test_invalid_asset_rejected_on_host(lib, field, value, needle):
 def test_null_arguments(lib):
     assert lib.esdp_create(None, 1, 0, None) == E.ESDP_EINVAL
     assert lib.esdp_solve(None, None, None, None, None, None, None) == E.ESDP_EINVAL
-    assert lib.esdp_grad(None, 0, None, None, None, None, None, None) == E.ESDP_EINVAL
+    assert lib.esdp_grad(None, 0, None, None, None, None, None, None, None, None, None,
+                         None) == E.ESDP_EINVAL
     assert lib.esdp_objective(None, 0, None, None, None) == E.ESDP_EINVAL
     lib.esdp_destroy(None)
 

@@ -256,7 +256,7 @@ def _gpu_full_policy(inst):
 
 def _grad_check(inst, tie_free):
     s, V1 = solve_gpu(inst)
-    J, dp, dt, de = s.grad(0, inst.mu0)
+    J, dp, dt, de, dco, dsw, dterm, dmu = s.grad(0, inst.mu0, extra=True)
     r = O.solve(inst, keep_V=True, nthreads=NTHREADS)
     scale = _scale(r["V1"])
     pol = _gpu_full_policy(inst)
@@ -265,7 +265,13 @@ def _grad_check(inst, tie_free):
     occ = O.occupancy(inst, pol, r["V"])
     assert J[0] == pytest.approx(occ["J"], rel=VTOL)
     checks = (("d_price", dp, "d_price"), ("d_trans", dt, "d_trans"),
-              ("d_eta_c", de[:1], "d_eta_c"), ("d_eta_d", de[1:], "d_eta_d"))
+              ("d_eta_c", de[:1], "d_eta_c"), ("d_eta_d", de[1:], "d_eta_d"),
+              ("d_cost", dco, "d_cost"), ("d_terminal", dterm, "d_terminal"),
+              ("d_mu0", dmu, "d_mu0"))
+    if inst.n_modes == 2:
+        checks += (("d_switch", dsw, "d_switch"),)
+    else:
+        assert dsw[0] == 0.0
     for name, g, key in checks:
         ref = np.atleast_1d(occ[key])
         err = np.abs(g.astype(np.float64).reshape(ref.shape) - ref).max() / max(np.abs(ref).max(), 1e-12)
@@ -475,7 +481,10 @@ def test_autograd_objective_matches_oracle_adjoint():
     trans = torch.tensor(inst.trans, device=dev, requires_grad=True)
     eta_c = torch.tensor(inst.eta_c, dtype=torch.float64, requires_grad=True)
     eta_d = torch.tensor(inst.eta_d, dtype=torch.float64, requires_grad=True)
-    J = f(price, trans, eta_c, eta_d)
+    cost = torch.tensor(inst.cost, device=dev, requires_grad=True)
+    terminal = torch.tensor(inst.terminal, device=dev, requires_grad=True)
+    mu0 = torch.tensor(inst.mu0, device=dev, requires_grad=True)
+    J = f(price, trans, eta_c, eta_d, cost=cost, terminal=terminal, mu0=mu0)
     # another solve in between: backward must recompute the first one
     J_other = f(price.detach() * 2, trans.detach())
     J.backward()
@@ -484,7 +493,8 @@ def test_autograd_objective_matches_oracle_adjoint():
     assert float(J_other) != pytest.approx(float(J.detach()), rel=1e-3)
     occ = O.occupancy(inst, r["policy"], r["V"])
     for g, key in ((price.grad, "d_price"), (trans.grad, "d_trans"),
-                   (eta_c.grad, "d_eta_c"), (eta_d.grad, "d_eta_d")):
+                   (eta_c.grad, "d_eta_c"), (eta_d.grad, "d_eta_d"), (cost.grad, "d_cost"),
+                   (terminal.grad, "d_terminal"), (mu0.grad, "d_mu0")):
         ref = np.atleast_1d(occ[key])
         got = g.detach().cpu().numpy().astype(np.float64).reshape(ref.shape)
         err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-12)
@@ -509,9 +519,11 @@ def test_autograd_checkpointed_int16():
     f = StorageObjective(inst)
     price = torch.tensor(inst.price, device=f.device, requires_grad=True)
     trans = torch.tensor(inst.trans, device=f.device, requires_grad=True)
-    f(price, trans).backward()
+    sw = torch.tensor(inst.switch_cost, dtype=torch.float64, requires_grad=True)
+    f(price, trans, switch_cost=sw).backward()
     s, _ = solve_gpu(inst)
-    J, dp, dt, de = s.grad(0, inst.mu0)
+    J, dp, dt, de, dco, dsw, dterm, dmu = s.grad(0, inst.mu0, extra=True)
+    assert float(sw.grad) == pytest.approx(dsw[0], rel=1e-6, abs=1e-12)
     # same adjoint; the occupancy sums use atomics, so the order of the
     # double additions (and the last float32 bit) may differ between runs
     np.testing.assert_allclose(price.grad.cpu().numpy(), dp, rtol=1e-6, atol=1e-6 * np.abs(dp).max())

@@ -504,6 +504,49 @@ def test_gradients_vs_central_differences(modes):
     assert fd == pytest.approx(occ["d_eta_d"], rel=1e-5, abs=1e-6)
 
 
+@pytest.mark.parametrize("modes", [1, 2])
+def test_input_gradients_vs_central_differences(modes):
+    """Per-action cost, switch cost, terminal value and initial price-state
+    distribution: central differences of the FP64 DP against the occupancy
+    pass (a planted sign error or a dropped term fails these)."""
+    inst = _tie_free(55, modes)
+    r, occ = _min_gap(inst)
+    cost = inst.cost.astype(np.float64)
+    h = 1e-4
+    chosen = np.unique(r["policy"])
+    unused = [a for a in range(inst.A) if a not in set(chosen.tolist())]
+    for a in list(chosen[:3]) + unused[:1]:
+        c1 = cost.copy(); c1[a] += h
+        c2 = cost.copy(); c2[a] -= h
+        fd = (_J(inst, cost=c1) - _J(inst, cost=c2)) / (2 * h)
+        assert fd == pytest.approx(occ["d_cost"][a], rel=1e-6, abs=1e-9)
+    assert any(occ["d_cost"][a] < 0 for a in chosen) and all(occ["d_cost"][a] == 0 for a in unused)
+    # the cost gradient counts every decision once: total occupancy mass
+    assert -occ["d_cost"].sum() == pytest.approx(occ["mass"].sum(), rel=1e-12)
+    if modes == 2:
+        hs = 1e-4
+        fd = (_J(inst, switch_cost=inst.switch_cost + hs)
+              - _J(inst, switch_cost=inst.switch_cost - hs)) / (2 * hs)
+        assert fd == pytest.approx(occ["d_switch"], rel=1e-6, abs=1e-9)
+    term = inst.terminal.astype(np.float64)
+    flat = np.argsort(-occ["d_terminal"].ravel())[:3]
+    for i in list(flat) + [int(np.argmin(occ["d_terminal"].ravel()))]:
+        idx = np.unravel_index(i, term.shape)
+        t1 = term.copy(); t1[idx] += h
+        t2 = term.copy(); t2[idx] -= h
+        fd = (_J(inst, terminal=t1) - _J(inst, terminal=t2)) / (2 * h)
+        assert fd == pytest.approx(occ["d_terminal"][idx], rel=1e-6, abs=1e-9)
+    # the final occupancy is a distribution (up to the float32 row sums of P)
+    rowdev = np.abs(inst.trans.astype(np.float64).sum(axis=2) - 1.0).max()
+    assert occ["d_terminal"].sum() == pytest.approx(1.0, abs=(inst.T + 1) * (rowdev + 1e-7))
+    # J is linear in mu0
+    import copy
+    for k in range(inst.K):
+        i1 = copy.copy(inst); i1.mu0 = inst.mu0.astype(np.float64).copy(); i1.mu0[k] += 0.5
+        assert O.objective(i1, r["V1"]) - O.objective(inst, r["V1"]) == pytest.approx(
+            0.5 * occ["d_mu0"][k], rel=1e-12, abs=1e-12)
+
+
 # --------------------------------------------------------------------- hull
 
 def _hull_brute(y):
