@@ -156,6 +156,44 @@ int esdp_status(esdp_ctx* ctx, void* stream);
 int esdp_launch_info(const esdp_ctx* ctx, int32_t* grid, int32_t* block, int32_t* items,
                      int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread);
 
+/* ---------------------------------------------------------------------
+ * Stagewise-independent prices on the paper's own action grid (Sec. III-A,
+ * Algorithm 1, eq. 2 and 13).  Per stage t = T..1:
+ *   V_{t-1}(s) = sum_k pi_hat[t][k] max_a ( lam_hat[t][k] p_a tau + V_t(sigma) ),
+ * actions p_a of eq. 13 (charge -p_max, -(n_c-1) delta/eta .. -delta/eta, idle
+ * 0, discharge delta eta .. (n_d-1) delta eta, p_max; n_c = ceil(p_max eta /
+ * delta), n_d = ceil(p_max / (delta eta)), delta = s_max/(S-1)), next state
+ * sigma = s delta + F(p_a) tau with F(p) = -p/eta (p >= 0) or -eta p (p < 0),
+ * V_t linearly interpolated between grid points off the grid, and -inf
+ * (infeasible) outside [0, s_max].  In the Markov form of esdp_solve this is
+ * the rank-1 transition P_t = 1 pi_hat_{t+1}^T with K = R price states.
+ * --------------------------------------------------------------------- */
+typedef struct {
+  int32_t T;             /* stages */
+  int32_t S;             /* SoC grid points */
+  int32_t R;             /* price samples per stage, 1..4096 */
+  int32_t policy_bytes;  /* 0 (values only), 2 or 4: argmax action index per (t, s, k) */
+  double s_max;          /* MWh */
+  double p_max;          /* MW */
+  double eta;            /* efficiency of eq. 2, in (0, 1] */
+  double tau;            /* stage length in hours */
+} esdp_iid_problem;
+
+/* The action grid of eq. 13 for a problem: writes the P power levels (MW,
+ * ascending) to p_hat when it is not NULL and their count to *n_actions. */
+int esdp_iid_actions(const esdp_iid_problem* problem, double* p_hat, int32_t* n_actions);
+
+/* Backward induction over all T stages in one persistent launch.
+ *   lam_hat, pi_hat [T][R]: price samples and probabilities of stages 1..T
+ *   terminal [S] V_T (NULL: zero); V0 [S] out: V_0
+ *   policy [T][S][R] int32/int16 as policy_bytes says (stage t at t-1) or NULL
+ * With flags & ESDP_DEVICE_PTRS the arrays are device pointers, else host
+ * arrays.  Allocates its workspace, blocks until done; returns ESDP_OK or a
+ * negative code with a message in err (err_len bytes, may be NULL). */
+int esdp_solve_iid(const esdp_iid_problem* problem, const float* lam_hat, const float* pi_hat,
+                   const float* terminal, float* V0, void* policy, uint32_t flags, void* stream,
+                   char* err, int32_t err_len);
+
 /* Allocation-free solve of one asset.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, for example a
  * plug-in running inside an application that owns the device memory pool

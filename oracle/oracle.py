@@ -230,12 +230,16 @@ def paper_F(p: np.ndarray, eta: float) -> np.ndarray:
 
 
 def paper_alg1(s_max: float, delta: float, p_max: float, eta: float, lam_hat: np.ndarray,
-               pi_hat: np.ndarray, snap: float = 1e-9):
+               pi_hat: np.ndarray, snap: float = 1e-9, *, terminal=None, tau: float = 1.0,
+               keep_policy: bool = False):
     """Algorithm 1 in numpy.
 
     lam_hat, pi_hat: [T, R] price samples and probabilities for stages 1..T.
     Returns V_hat [T+1, S]: V_hat[t] is the expected value vector
-    V_hat_t for t = 0..T (V_hat_T = 0, the base case).
+    V_hat_t for t = 0..T (V_hat_T = 0, the base case, or `terminal`).
+    Stages last `tau` hours (the paper's are hourly: tau = 1): payoff
+    lam * p * tau, SoC change F(p) * tau.  With keep_policy also the argmax
+    action index (first maximiser) and the top-two gap per [t-1, s, r].
 
     `snap` absorbs floating-point noise in sigma/delta so that states that
     the paper's recombining grid puts exactly on grid points are treated as
@@ -246,7 +250,7 @@ def paper_alg1(s_max: float, delta: float, p_max: float, eta: float, lam_hat: np
     s_hat = np.arange(S) * delta
     p_hat, _, _ = paper_action_grid(p_max, delta, eta)
     P = len(p_hat)
-    sigma = s_hat[:, None] + paper_F(p_hat, eta)[None, :]            # next-state levels
+    sigma = s_hat[:, None] + tau * paper_F(p_hat, eta)[None, :]      # next-state levels
     z = np.clip(sigma, 0.0, s_max) / delta + 1.0                       # next-state proxies
     zr = np.round(z)
     z = np.where(np.abs(z - zr) < snap, zr, z)
@@ -255,13 +259,25 @@ def paper_alg1(s_max: float, delta: float, p_max: float, eta: float, lam_hat: np
     b = np.where(zp > zm, (z - zm) / np.maximum(zp - zm, 1), 0.0)      # interpolation factors
     infeasible = (sigma < -snap * delta) | (sigma > s_max + snap * delta)
     V = np.zeros((T + 1, S))
+    if terminal is not None:
+        V[T] = np.asarray(terminal, dtype=np.float64)
+    pol = np.empty((T, S, R), np.int32) if keep_policy else None
+    gap = np.empty((T, S, R)) if keep_policy else None
+    lam64 = np.asarray(lam_hat, dtype=np.float64)
+    pi64 = np.asarray(pi_hat, dtype=np.float64)
     for t in range(T, 0, -1):
         Vt = V[t]
         Vnext = (1.0 - b) * Vt[zm - 1] + b * Vt[zp - 1]
         Vnext = np.where(infeasible, -np.inf, Vnext)
-        Qall = (p_hat[:, None] * lam_hat[t - 1][None, :])[None, :, :] + Vnext[:, :, None]
+        Qall = (tau * p_hat[:, None] * lam64[t - 1][None, :])[None, :, :] + Vnext[:, :, None]
         Q = Qall.max(axis=1)                                           # S x R
-        V[t - 1] = Q @ pi_hat[t - 1]
+        if keep_policy:
+            pol[t - 1] = Qall.argmax(axis=1)
+            top2 = np.partition(np.where(np.isfinite(Qall), Qall, -1e300), P - 2, axis=1)[:, P - 2, :]
+            gap[t - 1] = Q - top2
+        V[t - 1] = Q @ pi64[t - 1]
+    if keep_policy:
+        return V, pol, gap
     return V
 
 

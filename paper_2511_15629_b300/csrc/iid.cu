@@ -1,0 +1,480 @@
+// Stagewise-independent prices on the paper's own action grid (Sec. III-A,
+// Algorithm 1, eq. 2 and 13):
+//   V_{t-1}(s) = sum_k pi_t[k] max_a ( lam_t[k] p_a tau + V_t(sigma(s, a)) )
+// with R price samples (lam_t[k], pi_t[k]) per stage, the power actions p_a of
+// eq. 13 (grid steps delta*eta / delta/eta and the two end points -p_max,
+// +p_max), next state sigma = s delta + F(p_a) tau (F = -p/eta discharging,
+// -eta p charging), linear interpolation of V_t between the two neighbouring
+// grid points when sigma is off the grid, and -inf outside [0, s_max].
+//
+// In the Markov form of the main sweep this is the rank-1 transition
+// P_t[k][k2] = pi_{t+1}[k2]: the next-stage value is one vector over SoC for
+// every price sample, so a stage needs no K x K contraction, only one
+// weighted sum over the samples per SoC point.  This kernel exploits that:
+// a tile of SoC rows stages a single column of V_t (its rows plus the action
+// halo), forms the feasible, interpolated next values once per (row, action),
+// and every price sample of the row reuses them; a thread owns one row and
+// kIidKG samples and runs the max over all actions for them.
+//
+// Persistent cooperative launch over all stages; tiles synchronise with their
+// neighbours only (release/acquire flags, bounded waits) as in the main sweep.
+// Values are kept as V'_t = V_t - c_t in float32 with the scalar level c_t in
+// double (every stage re-centres on a reference row).
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/esdp.h"
+#include "esdp_internal.h"
+
+namespace esdp {
+namespace {
+
+constexpr int kIidBlock = 512;
+constexpr int kIidKG = 8;  // price samples per thread
+constexpr size_t kIidSmemLimit = 227 * 1024;
+
+struct IidParams {
+  int T, S, R, P, W, n_tiles, reach, groups;
+  int dmin, span;            // halo rows of a tile: [s0 + dmin, s0 + dmin + span)
+  int ref_tile, ref_row;
+  const float* lam;          // [T][R]
+  const float* pi;           // [T][R]
+  const double* rho;         // [T] sum_k pi_t[k]
+  const float* pay;          // [P] p_a * tau
+  const int* dlo;            // [P] floor of the SoC shift in grid steps
+  const float* bw;           // [P] weight of grid point dlo + 1 (0: on the grid)
+  const int* smin;           // [P] feasible rows s of action a: smin[a] <= s <= smax[a]
+  const int* smax;
+  const float* terminal;     // [S] V_T, or nullptr for 0
+  float* v;                  // [2][S] V'_t, t even / odd
+  float* ref_hist;           // [T+1] V'_t[ref_row]
+  int* flags;                // [n_tiles], zero at launch
+  int* status;
+  int* pol32;                // [T][S][R] argmax (action index) or nullptr
+  short* pol16;
+  float* v_out;              // [S] V_0
+  const int* cta_first;      // [grid+1] contiguous tile ranges
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Release the tile's values: the barrier orders every thread's stores before
+// thread 0's release store (cumulativity), consumers read after an acquire.
+__device__ __forceinline__ void publish(int* flag, int v) {
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(flag, v);
+}
+
+// Wait until the neighbour tiles within `reach` and the reference tile have
+// published at least `need` stages; the thread that waits for the reference
+// tile reads V'_t[ref].  Bounded: ESDP_ETIMEOUT in the status word and false.
+__device__ bool iid_wait(const IidParams& p, int tile, int need, int t, float* s_ref,
+                         int* s_abort) {
+  const int lo = max(0, tile - p.reach), hi = min(p.n_tiles - 1, tile + p.reach);
+  const int n = hi - lo + 1;
+  if ((int)threadIdx.x <= n) {
+    const int* f = p.flags + ((int)threadIdx.x < n ? lo + (int)threadIdx.x : p.ref_tile);
+    if (ld_acquire(f) < need) {
+      const unsigned long long t0 = now_ns();
+      for (unsigned it = 1;; ++it) {
+        if (ld_acquire(f) >= need) break;
+        if ((it & 15u) == 0) {
+          if (*(volatile int*)p.status != 0) {
+            *(volatile int*)s_abort = 1;
+            break;
+          }
+          if (now_ns() - t0 > p.timeout_ns) {
+            atomicCAS(p.status, 0, ESDP_ETIMEOUT);
+            *(volatile int*)s_abort = 1;
+            break;
+          }
+        }
+      }
+    }
+    if ((int)threadIdx.x == n) *s_ref = __ldcg(p.ref_hist + t);
+  }
+  __syncthreads();
+  return *(volatile int*)s_abort == 0;
+}
+
+template <bool kPol>
+__global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
+  extern __shared__ float4 ism4[];
+  float* ism = reinterpret_cast<float*>(ism4);
+  auto al = [](int x) { return (x + 31) & ~31; };
+  float* Vt = ism;                          // [span] halo column of V'_t - r_t
+  float* B = Vt + al(p.span);               // [W][P] next values of every (row, action)
+  float* pay = B + al(p.W * p.P);           // [P]
+  float* red = pay + al(p.P);               // [W][groups] per-group expectations
+  __shared__ float s_ref;
+  __shared__ int s_abort;
+  __shared__ double s_c;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int S = p.S, R = p.R, P = p.P, W = p.W, groups = p.groups;
+  const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
+  const float NEG = -CUDART_INF_F;
+  if (tid == 0) {
+    s_abort = 0;
+    s_c = 0.0;
+  }
+  for (int a = tid; a < P; a += nth) pay[a] = p.pay[a];
+  __syncthreads();
+
+  // prologue: V'_T = V_T (c_T = 0)
+  for (int tile = i0; tile < i1; ++tile) {
+    const int s0 = tile * W, s1 = min(S, s0 + W);
+    for (int s = s0 + tid; s < s1; s += nth) {
+      const float v = p.terminal ? __ldg(p.terminal + s) : 0.f;
+      p.v[(size_t)(p.T & 1) * S + s] = v;
+      if (s == p.ref_row) p.ref_hist[p.T] = v;
+    }
+    publish(p.flags + tile, 1);
+  }
+
+  const int rows_pass = nth / groups;  // rows of one pass of the max loop
+  const int my_row = tid / groups, my_group = tid - my_row * groups;
+  for (int g = 0; g < p.T; ++g) {
+    const int t = p.T - g;  // V'_{t-1} from V'_t
+    const float* vin = p.v + (size_t)(t & 1) * S;
+    float* vout = p.v + (size_t)((t - 1) & 1) * S;
+    const float* lam_t = p.lam + (size_t)(t - 1) * R;
+    const float* pi_t = p.pi + (size_t)(t - 1) * R;
+    for (int tile = i0; tile < i1; ++tile) {
+      const int s0 = tile * W, s1 = min(S, s0 + W), Wt = s1 - s0;
+      if (!iid_wait(p, tile, g + 1, t, &s_ref, &s_abort)) return;
+      const float r = s_ref;
+      if (tile == i0 && tid == 0) s_c = (s_c + (double)r) * p.rho[t - 1];  // c_{t-1}
+      // 1. halo column of V'_t, re-centred on the reference row
+      for (int i = tid; i < p.span; i += nth) {
+        const int row = s0 + p.dmin + i;
+        Vt[i] = (row >= 0 && row < S) ? __ldcg(vin + row) - r : 0.f;
+      }
+      __syncthreads();
+      // 2. next value of every (row, action): on the grid, interpolated, or
+      //    -inf when the next SoC leaves [0, s_max]
+      for (int i = tid; i < Wt * P; i += nth) {
+        const int rr = i / P, a = i - rr * P, s = s0 + rr;
+        float b = NEG;
+        if (s >= __ldg(p.smin + a) && s <= __ldg(p.smax + a)) {
+          const int j = s + __ldg(p.dlo + a) - (s0 + p.dmin);
+          const float w = __ldg(p.bw + a);
+          b = w == 0.f ? Vt[j] : fmaf(w, Vt[j + 1], (1.f - w) * Vt[j]);
+        }
+        B[rr * P + a] = b;
+      }
+      __syncthreads();
+      // 3. max over the actions for kIidKG price samples of one row; the
+      //    smallest maximising action index (strict >)
+      for (int rr = my_row; my_row < rows_pass && rr < Wt; rr += rows_pass) {
+        const int k0 = my_group * kIidKG;
+        float lam[kIidKG], best[kIidKG];
+        int arg[kIidKG];
+#pragma unroll
+        for (int j = 0; j < kIidKG; ++j) {
+          lam[j] = k0 + j < R ? __ldg(lam_t + k0 + j) : 0.f;
+          best[j] = NEG;
+          arg[j] = -1;
+        }
+        const float* Br = B + rr * P;
+        int a = 0;
+        if constexpr (!kPol) {
+          for (; a + 1 < P; a += 2) {
+            const float b0 = Br[a], b1 = Br[a + 1], p0 = pay[a], p1 = pay[a + 1];
+#pragma unroll
+            for (int j = 0; j < kIidKG; ++j)
+              best[j] = max3f(best[j], fmaf(lam[j], p0, b0), fmaf(lam[j], p1, b1));
+          }
+        }
+        for (; a < P; ++a) {
+          const float b0 = Br[a], p0 = pay[a];
+#pragma unroll
+          for (int j = 0; j < kIidKG; ++j) {
+            const float v = fmaf(lam[j], p0, b0);
+            if (kPol) {
+              if (v > best[j]) {
+                best[j] = v;
+                arg[j] = a;
+              }
+            } else {
+              best[j] = fmaxf(best[j], v);
+            }
+          }
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int j = 0; j < kIidKG; ++j)
+          if (k0 + j < R) part = fmaf(__ldg(pi_t + k0 + j), best[j], part);
+        red[rr * groups + my_group] = part;
+        if (kPol) {
+          const size_t base = ((size_t)(t - 1) * S + s0 + rr) * R + k0;
+#pragma unroll
+          for (int j = 0; j < kIidKG; ++j) {
+            if (k0 + j >= R) break;
+            if (p.pol32) p.pol32[base + j] = arg[j];
+            if (p.pol16) p.pol16[base + j] = (short)arg[j];
+          }
+        }
+      }
+      __syncthreads();
+      // 4. V'_{t-1}(s): the expectation over the samples, groups in order
+      for (int rr = tid; rr < Wt; rr += nth) {
+        float acc = 0.f;
+        for (int q = 0; q < groups; ++q) acc += red[rr * groups + q];
+        __stcg(vout + s0 + rr, acc);
+        if (s0 + rr == p.ref_row) __stcg(p.ref_hist + t - 1, acc);
+      }
+      publish(p.flags + tile, g + 2);
+    }
+  }
+  // V_0 = V'_0 + c_0
+  __syncthreads();
+  const double c = s_c;
+  for (int tile = i0; tile < i1; ++tile) {
+    const int s0 = tile * W, s1 = min(S, s0 + W);
+    for (int s = s0 + tid; s < s1; s += nth)
+      p.v_out[s] = (float)((double)__ldcg(p.v + s) + c);  // V'_0 sits in buffer 0
+  }
+}
+
+// rho_t = sum_k pi_t[k] in double
+__global__ void iid_rho_kernel(const float* pi, double* rho, int T, int R) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double acc = 0.0;
+  for (int k = 0; k < R; ++k) acc += (double)pi[(size_t)t * R + k];
+  rho[t] = acc;
+}
+
+int msg(char* buf, int32_t len, int code, const char* text) {
+  if (buf && len > 0) {
+    std::strncpy(buf, text, (size_t)len - 1);
+    buf[len - 1] = '\0';
+  }
+  return code;
+}
+
+// The action grid of eq. 13: -p_max, -(n_c-1) delta/eta, ..., -delta/eta, 0,
+// delta eta, ..., (n_d-1) delta eta, p_max with n_c = ceil(p_max eta/delta) and
+// n_d = ceil(p_max/(delta eta)).
+std::vector<double> action_grid(const esdp_iid_problem& q) {
+  const double delta = q.s_max / (double)(q.S - 1);
+  const int n_c = (int)std::ceil(q.p_max * q.eta / delta - 1e-12);
+  const int n_d = (int)std::ceil(q.p_max / (delta * q.eta) - 1e-12);
+  std::vector<double> p;
+  p.push_back(-q.p_max);
+  for (int j = n_c - 1; j >= 1; --j) p.push_back(-(double)j * delta / q.eta);
+  p.push_back(0.0);
+  for (int j = 1; j <= n_d - 1; ++j) p.push_back((double)j * delta * q.eta);
+  p.push_back(q.p_max);
+  return p;
+}
+
+}  // namespace
+}  // namespace esdp
+
+using namespace esdp;
+
+extern "C" int esdp_iid_actions(const esdp_iid_problem* q, double* p_hat, int32_t* n_actions) {
+  if (!q || !n_actions || q->S < 2 || !(q->s_max > 0) || !(q->p_max > 0) || !(q->eta > 0) ||
+      q->eta > 1 || !(q->tau > 0))
+    return ESDP_EINVAL;
+  const std::vector<double> p = action_grid(*q);
+  *n_actions = (int32_t)p.size();
+  if (p_hat) std::copy(p.begin(), p.end(), p_hat);
+  return ESDP_OK;
+}
+
+extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, const float* pi_hat,
+                              const float* terminal, float* V0, void* policy, uint32_t flags,
+                              void* stream, char* err, int32_t err_len) {
+  char buf[256];
+  if (!q || !lam_hat || !pi_hat || !V0) return msg(err, err_len, ESDP_EINVAL, "null argument");
+  if (q->T < 1 || q->S < 2 || q->R < 1 || q->R > kIidKG * kIidBlock)
+    return msg(err, err_len, ESDP_EINVAL, "T >= 1, S >= 2 and 1 <= R <= 4096 required");
+  if (!(q->s_max > 0) || !(q->p_max > 0) || !(q->eta > 0) || q->eta > 1 || !(q->tau > 0))
+    return msg(err, err_len, ESDP_EINVAL, "s_max, p_max, tau > 0 and 0 < eta <= 1 required");
+  if (q->policy_bytes != 0 && q->policy_bytes != 2 && q->policy_bytes != 4)
+    return msg(err, err_len, ESDP_EINVAL, "policy_bytes must be 0, 2 or 4");
+  if (q->policy_bytes && !policy)
+    return msg(err, err_len, ESDP_EINVAL, "policy_bytes > 0 needs a policy array");
+  const bool dev = (flags & ESDP_DEVICE_PTRS) != 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int T = q->T, S = q->S, R = q->R;
+  const double delta = q->s_max / (double)(S - 1);
+  const std::vector<double> p_hat = action_grid(*q);
+  const int P = (int)p_hat.size();
+  // per action: payoff coefficient, SoC shift f in grid steps (eq. 2), the
+  // grid point below and the interpolation weight (shifts within 1e-9 of a
+  // grid point are taken as on it), the feasible rows
+  std::vector<float> pay(P), bw(P);
+  std::vector<int> dlo(P), smin(P), smax(P);
+  int dmin = 0, dmax = 0;
+  for (int a = 0; a < P; ++a) {
+    const double pa = p_hat[a];
+    const double F = pa >= 0 ? -pa / q->eta : -q->eta * pa;
+    const double f = F * q->tau / delta;
+    double fl = std::floor(f), fr = f - fl;
+    if (fr < 1e-9) fr = 0.0;
+    if (fr > 1.0 - 1e-9) {
+      fr = 0.0;
+      fl += 1.0;
+    }
+    pay[a] = (float)(pa * q->tau);
+    dlo[a] = (int)fl;
+    bw[a] = (float)fr;
+    smin[a] = (int)std::ceil(-f - 1e-9);
+    smax[a] = (int)std::floor((double)(S - 1) - f + 1e-9);
+    dmin = std::min(dmin, dlo[a]);
+    dmax = std::max(dmax, dlo[a] + (fr > 0 ? 1 : 0));
+  }
+  const int groups = (R + kIidKG - 1) / kIidKG;
+  int dev_id = 0, n_sm = 0;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev_id);
+  const int w_max = kIidBlock / groups;
+  int W = std::max(1, std::min(w_max, (S + n_sm - 1) / n_sm));
+  auto smem_of = [&](int w) {
+    auto al = [](size_t x) { return (x + 31) / 32 * 32; };
+    const size_t span = (size_t)w + (size_t)(dmax - dmin) + 2;
+    return (al(span) + al((size_t)w * P) + al(P) + al((size_t)w * groups)) * sizeof(float);
+  };
+  while (W > 1 && smem_of(W) > kIidSmemLimit) --W;
+  if (smem_of(W) > kIidSmemLimit)
+    return msg(err, err_len, ESDP_EINVAL, "the action halo does not fit shared memory");
+  const int n_tiles = (S + W - 1) / W;
+  const int reach = (std::max(-dmin, dmax) + W - 1) / W;
+  if (2 * reach + 2 > kIidBlock) return msg(err, err_len, ESDP_EINVAL, "action halo too wide");
+
+  // workspace
+  std::vector<void*> allocs;
+  auto alloc = [&](void** p_, size_t bytes) {
+    if (cudaMalloc(p_, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(*p_);
+    return true;
+  };
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* a : allocs) cudaFree(a);
+  };
+  void *d_pay, *d_dlo, *d_bw, *d_smin, *d_smax, *d_v, *d_ref, *d_flags, *d_status, *d_rho, *d_cta;
+  void *d_lam = nullptr, *d_pi = nullptr, *d_term = nullptr, *d_v0 = nullptr, *d_pol = nullptr;
+  const size_t pol_bytes = (size_t)q->policy_bytes * T * S * R;
+  bool ok = alloc(&d_pay, P * 4) && alloc(&d_dlo, P * 4) && alloc(&d_bw, P * 4) &&
+            alloc(&d_smin, P * 4) && alloc(&d_smax, P * 4) && alloc(&d_v, (size_t)2 * S * 4) &&
+            alloc(&d_ref, (size_t)(T + 1) * 4) && alloc(&d_flags, (size_t)n_tiles * 4) &&
+            alloc(&d_status, 4) && alloc(&d_rho, (size_t)T * 8) &&
+            alloc(&d_cta, (size_t)(n_sm + 1) * 4);
+  if (ok && !dev) {
+    ok = alloc(&d_lam, (size_t)T * R * 4) && alloc(&d_pi, (size_t)T * R * 4) &&
+         alloc(&d_v0, (size_t)S * 4) && (!terminal || alloc(&d_term, (size_t)S * 4)) &&
+         (!q->policy_bytes || alloc(&d_pol, pol_bytes));
+  }
+  if (!ok) {
+    cleanup();
+    return msg(err, err_len, ESDP_ENOMEM, "device workspace allocation failed");
+  }
+  auto h2d = [&](void* d, const void* h, size_t n) {
+    return cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  ok = h2d(d_pay, pay.data(), P * 4) && h2d(d_dlo, dlo.data(), P * 4) &&
+       h2d(d_bw, bw.data(), P * 4) && h2d(d_smin, smin.data(), P * 4) &&
+       h2d(d_smax, smax.data(), P * 4);
+  if (ok && !dev) {
+    ok = h2d(d_lam, lam_hat, (size_t)T * R * 4) && h2d(d_pi, pi_hat, (size_t)T * R * 4) &&
+         (!terminal || h2d(d_term, terminal, (size_t)S * 4));
+  }
+  // launch shape: one CTA per SM at most, contiguous tile ranges
+  auto fn = policy && q->policy_bytes ? iid_kernel<true> : iid_kernel<false>;
+  const size_t smem = smem_of(W);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIidBlock, smem);
+  const int grid = std::max(1, std::min(n_tiles, std::min(n_sm, per_sm * n_sm)));
+  std::vector<int> cta(grid + 1);
+  for (int b = 0; b <= grid; ++b) cta[b] = (int)((long long)n_tiles * b / grid);
+  ok = ok && h2d(d_cta, cta.data(), (size_t)(grid + 1) * 4) &&
+       cudaMemsetAsync(d_flags, 0, (size_t)n_tiles * 4, st) == cudaSuccess &&
+       cudaMemsetAsync(d_status, 0, 4, st) == cudaSuccess;
+  if (!ok || per_sm < 1) {
+    cleanup();
+    return msg(err, err_len, ESDP_ECUDA, "workspace setup failed");
+  }
+  IidParams ip{};
+  ip.T = T; ip.S = S; ip.R = R; ip.P = P; ip.W = W; ip.n_tiles = n_tiles; ip.reach = reach;
+  ip.groups = groups;
+  ip.dmin = dmin;
+  ip.span = W + (dmax - dmin) + 2;
+  ip.ref_row = S / 2;
+  ip.ref_tile = ip.ref_row / W;
+  ip.lam = (const float*)(dev ? lam_hat : d_lam);
+  ip.pi = (const float*)(dev ? pi_hat : d_pi);
+  ip.rho = (const double*)d_rho;
+  ip.pay = (const float*)d_pay;
+  ip.dlo = (const int*)d_dlo;
+  ip.bw = (const float*)d_bw;
+  ip.smin = (const int*)d_smin;
+  ip.smax = (const int*)d_smax;
+  ip.terminal = dev ? terminal : (const float*)d_term;
+  ip.v = (float*)d_v;
+  ip.ref_hist = (float*)d_ref;
+  ip.flags = (int*)d_flags;
+  ip.status = (int*)d_status;
+  void* pol = dev ? policy : d_pol;
+  ip.pol32 = q->policy_bytes == 4 ? (int*)pol : nullptr;
+  ip.pol16 = q->policy_bytes == 2 ? (short*)pol : nullptr;
+  ip.v_out = dev ? V0 : (float*)d_v0;
+  ip.cta_first = (const int*)d_cta;
+  ip.timeout_ns = 5ull * 1000 * 1000 * 1000;
+  iid_rho_kernel<<<(T + 127) / 128, 128, 0, st>>>(ip.pi, (double*)d_rho, T, R);
+  void* args[] = {&ip};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kIidBlock), args,
+                                              smem, st);
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !dev) {
+    e = cudaMemcpyAsync(V0, d_v0, (size_t)S * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && q->policy_bytes)
+      e = cudaMemcpyAsync(policy, d_pol, pol_bytes, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) {
+    std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
+    return msg(err, err_len, ESDP_ECUDA, buf);
+  }
+  if (status) {
+    std::snprintf(buf, sizeof(buf), "device reported status %d", status);
+    return msg(err, err_len, status, buf);
+  }
+  return ESDP_OK;
+}

@@ -35,8 +35,8 @@ ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
-           "esdp_objective", "esdp_grad", "esdp_autotune", "esdp_status", "esdp_launch_info", "esdp_destroy",
-           "esdp_last_error", "esdp_version"]
+           "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_autotune",
+           "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
 
 
 class EsdpError(RuntimeError):
@@ -296,6 +296,65 @@ class Solver:
         self._check(self._lib.esdp_launch_info(self._ctx, *[ctypes.byref(v) for v in vals]))
         keys = ["grid", "block", "items", "rows_per_tile", "parts", "rows_per_thread"]
         return {k: v.value for k, v in zip(keys, vals)}
+
+
+class IidProblemC(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("S", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("policy_bytes", ctypes.c_int32), ("s_max", ctypes.c_double),
+                ("p_max", ctypes.c_double), ("eta", ctypes.c_double), ("tau", ctypes.c_double)]
+
+
+def _iid_struct(prob, policy_bytes=None) -> IidProblemC:
+    pb = prob.policy_bytes if policy_bytes is None else policy_bytes
+    return IidProblemC(prob.T, prob.S, prob.R, pb, prob.s_max, prob.p_max, prob.eta, prob.tau)
+
+
+def iid_actions(prob) -> np.ndarray:
+    """The power levels of eq. 13 (esdp_iid_actions), MW ascending."""
+    lib = load_library()
+    fn = lib.esdp_iid_actions
+    fn.argtypes = [ctypes.POINTER(IidProblemC), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    fn.restype = ctypes.c_int
+    q = _iid_struct(prob, 0)
+    n = ctypes.c_int32()
+    rc = fn(ctypes.byref(q), None, ctypes.byref(n))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, "invalid problem")
+    out = np.empty(n.value, np.float64)
+    fn(ctypes.byref(q), out.ctypes.data, ctypes.byref(n))
+    return out
+
+
+def solve_iid(prob, V0=None, policy=None, *, device=False, lam_hat=None, pi_hat=None,
+              terminal=None, policy_bytes=None, stream=None):
+    """Algorithm 1 on the GPU (esdp_solve_iid).  Host mode (default): numpy
+    in and out, returns V0 [S] (and the policy [T,S,R] when policy_bytes >
+    0).  Device mode: torch CUDA tensors (or raw device addresses) for
+    lam_hat, pi_hat, terminal, V0 and policy."""
+    lib = load_library()
+    fn = lib.esdp_solve_iid
+    fn.argtypes = [ctypes.POINTER(IidProblemC)] + [ctypes.c_void_p] * 5 + \
+        [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
+    fn.restype = ctypes.c_int
+    q = _iid_struct(prob, policy_bytes)
+    err = ctypes.create_string_buffer(512)
+    if device:
+        rc = fn(ctypes.byref(q), _dev_ptr(lam_hat), _dev_ptr(pi_hat), _dev_ptr(terminal),
+                _dev_ptr(V0), _dev_ptr(policy), ESDP_DEVICE_PTRS, _stream(stream), err, len(err))
+    else:
+        lam = np.ascontiguousarray(prob.lam_hat if lam_hat is None else lam_hat, np.float32)
+        pi = np.ascontiguousarray(prob.pi_hat if pi_hat is None else pi_hat, np.float32)
+        term = prob.terminal if terminal is None else terminal
+        term = None if term is None else np.ascontiguousarray(term, np.float32)
+        V0 = np.empty(prob.S, np.float32) if V0 is None else V0
+        if q.policy_bytes and policy is None:
+            policy = np.empty((prob.T, prob.S, prob.R), np.int16 if q.policy_bytes == 2 else np.int32)
+        rc = fn(ctypes.byref(q), lam.ctypes.data, pi.ctypes.data,
+                None if term is None else term.ctypes.data, V0.ctypes.data,
+                None if policy is None else policy.ctypes.data, 0, _stream(stream), err, len(err))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, err.value.decode())
+    return (V0, policy) if q.policy_bytes else V0
 
 
 def solve_noalloc(inst, price, trans, cost, terminal, V1, policy=None, stream=None) -> None:

@@ -372,3 +372,69 @@ def iid_instance(seed: int, T: int, N: int, R: int, D_dis: int, D_chg: int,
     inst.mu0 = np.ascontiguousarray(pis[0].copy())
     inst.meta["pi_hat"] = pis
     return inst
+
+
+# --------------------------------------------------------------------------
+# The paper's own setting: stagewise-independent price samples, eq. 13 grid
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class IidProblem:
+    """Algorithm 1 input: R price samples (lam_hat, pi_hat) per stage for a
+    storage of s_max MWh on an S-point SoC grid with power limit p_max and the
+    single efficiency eta of eq. 2; hourly stages by default."""
+    name: str
+    T: int
+    S: int
+    R: int
+    s_max: float
+    p_max: float
+    eta: float
+    lam_hat: np.ndarray      # [T, R] float32, $/MWh
+    pi_hat: np.ndarray       # [T, R] float32, rows sum to 1 (rounded)
+    tau: float = 1.0
+    terminal: Optional[np.ndarray] = None   # [S] float32 or None (zero, as in the paper)
+    policy_bytes: int = 0
+
+    @property
+    def delta(self) -> float:
+        return self.s_max / (self.S - 1)
+
+
+def iid_problem(seed: int, T: int, S: int, R: int, hours: float, *, p_max: float = 1.0,
+                eta: float = math.sqrt(0.85), neg_prob: float = 0.03,
+                weights: str = "uniform", terminal: bool = False,
+                name: str = "iid") -> IidProblem:
+    """Synthetic stand-in for the paper's real-time price samples (Sec. IV):
+    per stage R samples around a daily mean profile (40 +- 15 $/MWh with an
+    evening peak), lognormal spread sigma 0.35, a few negative prices
+    (probability neg_prob, down to -$30), uniform sample weights (as the
+    paper's empirical samples) or Dirichlet ones.  s_max = hours * p_max."""
+    rng = np.random.default_rng(seed)
+    h = np.arange(T) % 24
+    mean = 40.0 + 15.0 * np.sin(2 * np.pi * (h - 9) / 24.0) + 10.0 * np.exp(-0.5 * ((h - 18) / 2.0) ** 2)
+    lam = mean[:, None] * np.exp(rng.normal(0.0, 0.35, size=(T, R)) - 0.5 * 0.35 ** 2)
+    neg = rng.random((T, R)) < neg_prob
+    lam = np.where(neg, -rng.uniform(0.0, 30.0, size=(T, R)), lam)
+    if weights == "uniform":
+        pi = np.full((T, R), 1.0 / R)
+    else:
+        pi = rng.dirichlet(np.full(R, 1.0), size=T)
+    term = None
+    if terminal:
+        term = (25.0 * np.linspace(0.0, hours * p_max, S)).astype(np.float32)
+    return IidProblem(name, T, S, R, float(hours * p_max), float(p_max), float(eta),
+                      np.ascontiguousarray(lam.astype(np.float32)),
+                      _renorm_rows_f32(pi), terminal=term)
+
+
+# The six storage/grid combinations of the paper's runtime study (Table III):
+# (duration hours, S, P) with p_max = 1 MW, eta = sqrt(0.85), R = 200 samples,
+# T = 8784 hourly stages.
+TABLE3_CASES = [(4, 41, 22), (20, 201, 22), (100, 1001, 22), (4, 401, 203), (20, 2001, 203),
+                (100, 10001, 203)]
+
+
+def table3_problem(case: int, seed: int = 3000, T: int = 8784, R: int = 200) -> IidProblem:
+    hours, S, _ = TABLE3_CASES[case]
+    return iid_problem(seed + case, T, S, R, hours, name=f"table3-{hours}h-S{S}")

@@ -1,10 +1,12 @@
 """C-ABI library: loads without a GPU, exports every symbol include/*.h
 declares, validates arguments on the host before touching the device."""
 import ctypes
+import dataclasses
 import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2511_15629_b300 import build as B
@@ -84,3 +86,50 @@ def test_allocation_failure_injection(lib, monkeypatch):
     a = E.asset_from_instance(I.random_instance(0, 3, 20, 4, 2, 3))
     rc, msg = _create(lib, a)
     assert rc == E.ESDP_ENOMEM and "injected" in msg
+
+
+# ------------------------------------------------ stagewise-independent path
+
+def test_iid_struct_layout_matches_header():
+    # 4 int32 followed by 4 doubles
+    assert ctypes.sizeof(E.IidProblemC) == 4 * 4 + 4 * 8
+    assert E.IidProblemC.s_max.offset == 16
+
+
+def _golden(name):
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def test_iid_action_grid_matches_tables_and_oracle(lib):
+    """The library's eq. 13 grid (computed on the host, no GPU) has the
+    action counts of Tables I and III and the oracle's levels."""
+    import math
+    from oracle import oracle as O
+    from paper_2511_15629_b300 import instances as I
+    eta = math.sqrt(0.85)
+    for dur, delta, S, P in _golden("table3_grid_sizes.txt"):
+        prob = I.IidProblem("t3", 1, int(S), 1, dur, 1.0, eta, None, None)
+        p = E.iid_actions(prob)
+        assert len(p) == int(P)
+        ref, _, _ = O.paper_action_grid(1.0, dur / (S - 1), eta)
+        np.testing.assert_allclose(p, ref, rtol=0, atol=1e-12)
+    for delta, P in _golden("table1_action_counts.txt"):
+        prob = I.IidProblem("t1", 1, int(round(4.0 / delta)) + 1, 1, 4.0, 1.0, eta, None, None)
+        assert len(E.iid_actions(prob)) == int(P)
+
+
+def test_iid_rejects_bad_problems(lib):
+    from paper_2511_15629_b300 import instances as I
+    prob = I.iid_problem(1, 3, 11, 4, 1.0)
+    for field, value in [("eta", 1.5), ("S", 1), ("R", 0), ("policy_bytes", 3), ("tau", 0.0)]:
+        bad = dataclasses.replace(prob, **{field: value})
+        with pytest.raises(E.EsdpError) as ei:
+            E.solve_iid(bad, policy_bytes=getattr(bad, "policy_bytes"))
+        assert ei.value.code == E.ESDP_EINVAL
