@@ -496,7 +496,42 @@ def bench_config5(torch, E, I, stream, flush, args, n_sm, f_max):
             "plain_evals_per_s": inst.evals * n / t_plain}
 
 
-EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5}
+# The paper's own runtime study (Table III): seconds on an L40S GPU (CuPy)
+# and on a 32-core Xeon (NumPy) for T = 8784 hourly stages, R = 200 price
+# samples; context only (other hardware, ISO-NE data not available here).
+TABLE3_PAPER_GPU_S = [2.77, 2.81, 2.94, 4.88, 19.17, 86.67]
+TABLE3_PAPER_CPU_S = [3.98, 18.29, 98.12, 397.80, 1996.02, 9972.64]
+
+
+def bench_table3(torch, E, I, stream, flush, args, n_sm, f_max):
+    """Algorithm 1 on the Table III shapes (esdp_solve_iid, values only):
+    wall time of the blocking call (workspace allocation included), inputs
+    already on the device."""
+    out = []
+    for case in range(len(I.TABLE3_CASES)):
+        prob = I.table3_problem(case)
+        lam = torch.from_numpy(prob.lam_hat).cuda()
+        pi = torch.from_numpy(prob.pi_hat).cuda()
+        V0 = torch.empty(prob.S, device="cuda")
+        P = len(E.iid_actions(prob))
+        evals = prob.T * prob.S * P * prob.R
+        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out.append({"case": prob.name, "T": prob.T, "S": prob.S, "P": P, "R": prob.R,
+                    "evals": evals, "seconds": sec, "evals_per_s": evals / sec,
+                    "frac_alu": evals / sec / alu_peak_evals(n_sm, f_max),
+                    "paper_gpu_s_l40s": TABLE3_PAPER_GPU_S[case],
+                    "paper_cpu_s_xeon32": TABLE3_PAPER_CPU_S[case],
+                    "speedup_vs_paper_gpu": TABLE3_PAPER_GPU_S[case] / sec})
+    return out
+
+
+EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
+          "paper_table3": bench_table3}
 
 
 def run_profile_case(name):
