@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
   extern __shared__ float4 ism4[];
   float* ism = reinterpret_cast<float*>(ism4);
   auto al = [](int x) { return (x + 31) & ~31; };
+  const int Pp = (p.P + 3) & ~3;            // actions padded to a multiple of 4
   float* Vt = ism;                          // [span] halo column of V'_t - r_t
-  float* B = Vt + al(p.span);               // [W][P] next values of every (row, action)
-  float* pay = B + al(p.W * p.P);           // [P]
+  float2* BP = reinterpret_cast<float2*>(Vt + al(p.span));  // [W][Pp] (next value, payoff)
+  float* pay = reinterpret_cast<float*>(BP + (size_t)p.W * Pp);  // [P]
   float* red = pay + al(p.P);               // [W][groups] per-group expectations
   __shared__ float s_ref;
   __shared__ int s_abort;
@@ -179,15 +180,18 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
       __syncthreads();
       // 2. next value of every (row, action): on the grid, interpolated, or
       //    -inf when the next SoC leaves [0, s_max]
-      for (int i = tid; i < Wt * P; i += nth) {
-        const int rr = i / P, a = i - rr * P, s = s0 + rr;
-        float b = NEG;
-        if (s >= __ldg(p.smin + a) && s <= __ldg(p.smax + a)) {
-          const int j = s + __ldg(p.dlo + a) - (s0 + p.dmin);
-          const float w = __ldg(p.bw + a);
-          b = w == 0.f ? Vt[j] : fmaf(w, Vt[j + 1], (1.f - w) * Vt[j]);
+      for (int i = tid; i < Wt * Pp; i += nth) {
+        const int rr = i / Pp, a = i - rr * Pp, s = s0 + rr;
+        float b = NEG, pa = 0.f;  // padding actions: -inf
+        if (a < P) {
+          pa = pay[a];
+          if (s >= __ldg(p.smin + a) && s <= __ldg(p.smax + a)) {
+            const int j = s + __ldg(p.dlo + a) - (s0 + p.dmin);
+            const float w = __ldg(p.bw + a);
+            b = w == 0.f ? Vt[j] : fmaf(w, Vt[j + 1], (1.f - w) * Vt[j]);
+          }
         }
-        B[rr * P + a] = b;
+        BP[rr * Pp + a] = make_float2(b, pa);
       }
       __syncthreads();
       // 3. max over the actions for kIidKG price samples of one row; the
@@ -202,28 +206,29 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
           best[j] = NEG;
           arg[j] = -1;
         }
-        const float* Br = B + rr * P;
-        int a = 0;
+        const float2* Br = BP + rr * Pp;
         if constexpr (!kPol) {
-          for (; a + 1 < P; a += 2) {
-            const float b0 = Br[a], b1 = Br[a + 1], p0 = pay[a], p1 = pay[a + 1];
+          // four actions per step: two 16-byte reads of (next value, payoff)
+          const float4* B4 = reinterpret_cast<const float4*>(Br);
+#pragma unroll 2
+          for (int q = 0; q < (Pp >> 1); q += 2) {
+            const float4 x = B4[q], y = B4[q + 1];
 #pragma unroll
-            for (int j = 0; j < kIidKG; ++j)
-              best[j] = max3f(best[j], fmaf(lam[j], p0, b0), fmaf(lam[j], p1, b1));
+            for (int j = 0; j < kIidKG; ++j) {
+              best[j] = max3f(best[j], fmaf(lam[j], x.y, x.x), fmaf(lam[j], x.w, x.z));
+              best[j] = max3f(best[j], fmaf(lam[j], y.y, y.x), fmaf(lam[j], y.w, y.z));
+            }
           }
-        }
-        for (; a < P; ++a) {
-          const float b0 = Br[a], p0 = pay[a];
+        } else {
+          for (int a = 0; a < P; ++a) {
+            const float2 bp = Br[a];
 #pragma unroll
-          for (int j = 0; j < kIidKG; ++j) {
-            const float v = fmaf(lam[j], p0, b0);
-            if (kPol) {
+            for (int j = 0; j < kIidKG; ++j) {
+              const float v = fmaf(lam[j], bp.y, bp.x);
               if (v > best[j]) {
                 best[j] = v;
                 arg[j] = a;
               }
-            } else {
-              best[j] = fmaxf(best[j], v);
             }
           }
         }
@@ -358,12 +363,15 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
   int dev_id = 0, n_sm = 0;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev_id);
-  const int w_max = kIidBlock / groups;
-  int W = std::max(1, std::min(w_max, (S + n_sm - 1) / n_sm));
+  // one tile per SM where shared memory allows (rows beyond one pass of the
+  // block are taken in further passes): the per-tile wait, halo load and
+  // barriers then occur once per CTA and stage
+  int W = std::max(1, (S + n_sm - 1) / n_sm);
   auto smem_of = [&](int w) {
     auto al = [](size_t x) { return (x + 31) / 32 * 32; };
     const size_t span = (size_t)w + (size_t)(dmax - dmin) + 2;
-    return (al(span) + al((size_t)w * P) + al(P) + al((size_t)w * groups)) * sizeof(float);
+    const size_t Pp = (size_t)(P + 3) / 4 * 4;
+    return (al(span) + 2 * (size_t)w * Pp + al(P) + al((size_t)w * groups)) * sizeof(float);
   };
   while (W > 1 && smem_of(W) > kIidSmemLimit) --W;
   if (smem_of(W) > kIidSmemLimit)

@@ -103,3 +103,10 @@ def test_iid_equals_markov_sweep_on_recombining_grid():
     Vm = V1[0].astype(np.float64) @ prob.pi_hat[0].astype(np.float64)
     scale = max(np.abs(Vm).max(), 1.0)
     assert np.abs(V0 - Vm).max() / scale <= 2e-5
+
+
+def test_iid_tiles_taller_than_one_pass():
+    """S = 10001 on 148 SMs gives 68-row tiles while 64 samples per row fill
+    only 64 rows per pass of the block: rows are taken in two passes."""
+    prob = I.iid_problem(10, 6, 10001, 64, 1000.0)
+    _check_values(E.solve_iid(prob), _oracle(prob)[0])
