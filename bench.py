@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-case", default="",
-                    help="config3-64 | config2: one solve inside the NVTX range 'esdp_profile' "
+                    help="config3-64 | config2 | table3-20h: one solve inside the NVTX range 'esdp_profile' "
                          "(for ncu --nvtx --nvtx-include esdp_profile/)")
     return ap.parse_args()
 
@@ -549,6 +549,20 @@ def run_profile_case(name):
                           full.terminal, s0=full.s0)
     elif name == "config2":
         inst = I.config2()
+    elif name == "table3-20h":
+        # the stagewise-independent path on the 20 h / S = 2001 / P = 203 shape
+        prob = I.table3_problem(4)
+        lam = torch.from_numpy(prob.lam_hat).cuda()
+        pi = torch.from_numpy(prob.pi_hat).cuda()
+        V0 = torch.empty(prob.S, device="cuda")
+        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("esdp_profile")
+        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "S": prob.S, "R": prob.R, "T": prob.T}))
+        return
     else:
         raise SystemExit(f"unknown profile case {name}")
     d = {k: torch.from_numpy(v).to("cuda") for k, v in E.concat_inputs([inst]).items()}
