@@ -186,13 +186,45 @@ int esdp_iid_actions(const esdp_iid_problem* problem, double* p_hat, int32_t* n_
 /* Backward induction over all T stages in one persistent launch.
  *   lam_hat, pi_hat [T][R]: price samples and probabilities of stages 1..T
  *   terminal [S] V_T (NULL: zero); V0 [S] out: V_0
+ *   V_all [T+1][S] out: V_t of every stage t = 0..T (the input of
+ *     esdp_iid_bids and esdp_iid_clear), or NULL
  *   policy [T][S][R] int32/int16 as policy_bytes says (stage t at t-1) or NULL
  * With flags & ESDP_DEVICE_PTRS the arrays are device pointers, else host
  * arrays.  Allocates its workspace, blocks until done; returns ESDP_OK or a
  * negative code with a message in err (err_len bytes, may be NULL). */
 int esdp_solve_iid(const esdp_iid_problem* problem, const float* lam_hat, const float* pi_hat,
-                   const float* terminal, float* V0, void* policy, uint32_t flags, void* stream,
-                   char* err, int32_t err_len);
+                   const float* terminal, float* V0, float* V_all, void* policy, uint32_t flags,
+                   void* stream, char* err, int32_t err_len);
+
+/* Convexified price-quantity bid curves of the paper (eq. 8-11): for every
+ * delivery interval t in [t0, t1) and grid SoC s (the state s_{t-1}), the
+ * upper concave envelope over the power levels p_a of U_t(p_a; s) =
+ * V_t(s delta + F(p_a) tau) on the feasible actions (V_t interpolated off the
+ * grid).  Outputs, with n = t1 - t0 (device pointers; V_all as written by
+ * esdp_solve_iid):
+ *   n_bp      [n][S]     vertex count
+ *   bp_action [n][S][P]  action indices of the vertices, ascending power
+ *   bp_price  [n][S][P]  bid price of the segment between vertices q and q+1,
+ *                        -(U_{q+1} - U_q) / ((p_{q+1} - p_q) tau) in $/MWh,
+ *                        non-decreasing in q (monotone bids)
+ * The orientation test (y_j - y_i)(x_l - x_i) - (y_l - y_i)(x_j - x_i) <= 0
+ * drops a point (collinear points are dropped) and runs in double with
+ * round-to-nearest operations in that order.  Blocks until done. */
+int esdp_iid_bids(const esdp_iid_problem* problem, const float* V_all, int32_t t0, int32_t t1,
+                  int32_t* n_bp, int32_t* bp_action, float* bp_price, void* stream, char* err,
+                  int32_t err_len);
+
+/* Merit-order clearing of a price-taking storage against realised price
+ * paths (device pointers): lam_real [n_paths][T]; starting SoC s0 (MWh).
+ * At stage t the cleared power maximises lam_t p tau + V_t(s + F(p) tau)
+ * over the feasible actions (a vertex of the stage's convexified bid curve;
+ * the first on ties), the SoC moves (off the grid at the end-point actions)
+ * and lam_t p tau accrues.  Outputs: revenue [n_paths] and s_end [n_paths]
+ * (grid steps, double; may be NULL), actions [n_paths][T] or NULL.  Double
+ * arithmetic.  Blocks until done. */
+int esdp_iid_clear(const esdp_iid_problem* problem, const float* V_all, const float* lam_real,
+                   int32_t n_paths, double s0, double* revenue, double* s_end, int32_t* actions,
+                   void* stream, char* err, int32_t err_len);
 
 /* Allocation-free solve of one asset.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, for example a

@@ -282,6 +282,89 @@ def paper_alg1(s_max: float, delta: float, p_max: float, eta: float, lam_hat: np
 
 
 # --------------------------------------------------------------------------
+# Bid curves (eq. 8-11) and merit-order clearing on Algorithm 1's values
+# --------------------------------------------------------------------------
+
+def _v_at(v: np.ndarray, z: float) -> float:
+    """V at SoC position z (grid steps): the grid value within 1e-9 of a grid
+    point, else linear interpolation (1 - b) V[j] + b V[j+1]."""
+    S = len(v)
+    j = math.floor(z)
+    b = z - j
+    if b < 1e-9:
+        return float(np.float64(v[max(0, min(S - 1, j))]))
+    if b > 1.0 - 1e-9:
+        return float(np.float64(v[max(0, min(S - 1, j + 1))]))
+    return (1.0 - b) * float(v[j]) + b * float(v[j + 1])
+
+
+def _shifts(S: int, s_max: float, p_max: float, eta: float, tau: float):
+    delta = s_max / (S - 1)
+    p_hat, _, _ = paper_action_grid(p_max, delta, eta)
+    f = [float(x) * tau / delta for x in paper_F(p_hat, eta)]
+    return [float(x) for x in p_hat], f
+
+
+def paper_bids(S: int, s_max: float, p_max: float, eta: float, tau: float, v: np.ndarray, s: int):
+    """Convexified bid curve at grid SoC s from the next-stage values v [S]
+    (eq. 8-11): points (p_a, U(p_a; s) = V(s + F(p_a) tau)) of the feasible
+    actions, upper concave envelope by the monotone chain over ascending p (a
+    middle point is dropped when (y_j - y_i)(x_l - x_i) - (y_l - y_i)(x_j - x_i)
+    <= 0), bid prices -(dU/dp)/tau per envelope segment.  Returns (vertex
+    action indices, prices)."""
+    p, f = _shifts(S, s_max, p_max, eta, tau)
+    pts = []
+    for a in range(len(p)):
+        z = s + f[a]
+        if -1e-9 <= z <= S - 1 + 1e-9:
+            pts.append((a, p[a], _v_at(v, z)))
+    hull = []
+    for a, x, y in pts:
+        while len(hull) >= 2:
+            (_, xi, yi), (_, xj, yj) = hull[-2], hull[-1]
+            if (yj - yi) * (x - xi) - (y - yi) * (xj - xi) > 0.0:
+                break
+            hull.pop()
+        hull.append((a, x, y))
+    idx = [h[0] for h in hull]
+    prices = [-(hull[q + 1][2] - hull[q][2]) / ((hull[q + 1][1] - hull[q][1]) * tau)
+              for q in range(len(hull) - 1)]
+    return idx, prices
+
+
+def paper_clear(S: int, s_max: float, p_max: float, eta: float, tau: float, V_all: np.ndarray,
+                lam_real: np.ndarray, s0: float):
+    """Merit-order clearing of a price-taking storage (Sec. V): at stage t the
+    cleared action maximises lam_t p tau + V_t(s + F(p) tau) (the vertex of
+    the convexified bid curve crossed by lam_t; the first on ties), the SoC
+    moves, lam_t p tau accrues.  Returns (revenue, final SoC in grid steps,
+    actions)."""
+    p, f = _shifts(S, s_max, p_max, eta, tau)
+    z = s0 / (s_max / (S - 1))
+    rev = 0.0
+    acts = []
+    T = len(lam_real)
+    for t in range(1, T + 1):
+        v = V_all[t]
+        lam = float(lam_real[t - 1])
+        best, arg = -math.inf, -1
+        for a in range(len(p)):
+            zn = z + f[a]
+            if not (-1e-9 <= zn <= S - 1 + 1e-9):
+                continue
+            val = lam * (p[a] * tau) + _v_at(v, zn)
+            if val > best:
+                best, arg = val, a
+        rev = rev + lam * (p[arg] * tau)
+        z = z + f[arg]
+        zr = float(np.rint(z))
+        if abs(z - zr) < 1e-9:
+            z = zr
+        acts.append(arg)
+    return rev, z, np.array(acts, np.int32)
+
+
+# --------------------------------------------------------------------------
 # Monte Carlo forward simulation of a policy
 # --------------------------------------------------------------------------
 

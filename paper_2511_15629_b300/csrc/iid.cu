@@ -59,6 +59,7 @@ struct IidParams {
   int* pol32;                // [T][S][R] argmax (action index) or nullptr
   short* pol16;
   float* v_out;              // [S] V_0
+  float* v_all;              // [T+1][S] V_t of every stage, or nullptr
   const int* cta_first;      // [grid+1] contiguous tile ranges
   unsigned long long timeout_ns;
 };
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
     for (int s = s0 + tid; s < s1; s += nth) {
       const float v = p.terminal ? __ldg(p.terminal + s) : 0.f;
       p.v[(size_t)(p.T & 1) * S + s] = v;
+      if (p.v_all) p.v_all[(size_t)p.T * S + s] = v;
       if (s == p.ref_row) p.ref_hist[p.T] = v;
     }
     publish(p.flags + tile, 1);
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
         float acc = 0.f;
         for (int q = 0; q < groups; ++q) acc += red[rr * groups + q];
         __stcg(vout + s0 + rr, acc);
+        if (p.v_all) p.v_all[(size_t)(t - 1) * S + s0 + rr] = (float)((double)acc + s_c);
         if (s0 + rr == p.ref_row) __stcg(p.ref_hist + t - 1, acc);
       }
       publish(p.flags + tile, g + 2);
@@ -266,6 +269,103 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
     for (int s = s0 + tid; s < s1; s += nth)
       p.v_out[s] = (float)((double)__ldcg(p.v + s) + c);  // V'_0 sits in buffer 0
   }
+}
+
+// ---- bid curves (eq. 8-11) and market clearing on the kept values
+
+struct IidActions {  // per action, in double
+  const double* p;   // power level (MW)
+  const double* f;   // SoC shift in grid steps F(p) tau / delta
+  int P, S;
+  double tau;
+};
+
+// V_t at SoC position z (grid steps; feasible when -1e-9 <= z <= S-1+1e-9):
+// the grid value within 1e-9 of a grid point, else linear interpolation,
+// in double with round-to-nearest operations in a fixed order.
+__device__ __forceinline__ double v_at(const float* v, int S, double z) {
+  double j = floor(z);
+  double b = __dsub_rn(z, j);
+  if (b < 1e-9) return (double)v[max(0, min(S - 1, (int)j))];
+  if (b > 1.0 - 1e-9) return (double)v[max(0, min(S - 1, (int)j + 1))];
+  const int i = (int)j;
+  return __dadd_rn(__dmul_rn(__dsub_rn(1.0, b), (double)v[i]), __dmul_rn(b, (double)v[i + 1]));
+}
+
+__device__ __forceinline__ bool feasible(double z, int S) {
+  return z >= -1e-9 && z <= (double)(S - 1) + 1e-9;
+}
+
+// Upper concave envelope over the power levels of U(p_a) = V_t(s + f_a) for
+// the feasible actions at grid SoC s (monotone chain, ascending p; a middle
+// point is dropped when (y_j - y_i)(x_l - x_i) - (y_l - y_i)(x_j - x_i) <= 0 in
+// double); bid price of segment q: -(y_{q+1} - y_q) / ((x_{q+1} - x_q) tau).
+__global__ void iid_bids_kernel(const IidActions A, const float* v_all, int t0, int n_t,
+                                int* n_bp, int* bp_action, float* bp_price) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)n_t * A.S) return;
+  const int tt = (int)(id / A.S), s = (int)(id - (long long)tt * A.S);
+  const float* v = v_all + (size_t)(t0 + tt) * A.S;
+  int* stk = bp_action + (size_t)id * A.P;
+  auto y_of = [&](int a) { return v_at(v, A.S, __dadd_rn((double)s, A.f[a])); };
+  int nh = 0;
+  for (int l = 0; l < A.P; ++l) {
+    if (!feasible(__dadd_rn((double)s, A.f[l]), A.S)) continue;
+    const double xl = A.p[l], yl = y_of(l);
+    while (nh >= 2) {
+      const int i = stk[nh - 2], j = stk[nh - 1];
+      const double xi = A.p[i], yi = y_of(i), xj = A.p[j], yj = y_of(j);
+      const double cross = __dsub_rn(__dmul_rn(__dsub_rn(yj, yi), __dsub_rn(xl, xi)),
+                                     __dmul_rn(__dsub_rn(yl, yi), __dsub_rn(xj, xi)));
+      if (cross > 0.0) break;
+      --nh;
+    }
+    stk[nh++] = l;
+  }
+  n_bp[id] = nh;
+  float* pr = bp_price + (size_t)id * A.P;
+  for (int q = 0; q + 1 < nh; ++q) {
+    const int a = stk[q], b = stk[q + 1];
+    const double dy = __dsub_rn(y_of(b), y_of(a));
+    pr[q] = (float)(-__ddiv_rn(dy, __dmul_rn(__dsub_rn(A.p[b], A.p[a]), A.tau)));
+  }
+}
+
+// Merit-order clearing of a price-taking storage against realised prices: at
+// stage t the cleared power maximises lam_t p tau + U_t(p; s) over the
+// actions (the vertex of the convexified bid curve where the bid price
+// crosses lam_t; the first such action on ties), the SoC moves by F(p) tau
+// (off the grid at the end points: V_t interpolated there) and the revenue
+// lam_t p tau accrues.  One thread per price path.
+__global__ void iid_clear_kernel(const IidActions A, const float* v_all, int T, const float* lam,
+                                 int n_paths, double s0, double* revenue, double* s_end,
+                                 int* actions) {
+  const int path = blockIdx.x * blockDim.x + threadIdx.x;
+  if (path >= n_paths) return;
+  double z = s0, rev = 0.0;
+  for (int t = 1; t <= T; ++t) {
+    const float* v = v_all + (size_t)t * A.S;
+    const double l = (double)lam[(size_t)path * T + t - 1];
+    double best = -INFINITY;
+    int arg = -1;
+    for (int a = 0; a < A.P; ++a) {
+      const double zn = __dadd_rn(z, A.f[a]);
+      if (!feasible(zn, A.S)) continue;
+      const double val = __dadd_rn(__dmul_rn(l, __dmul_rn(A.p[a], A.tau)), v_at(v, A.S, zn));
+      if (val > best) {
+        best = val;
+        arg = a;
+      }
+    }
+    if (arg < 0) arg = 0;  // not reached: idle is always feasible
+    rev = __dadd_rn(rev, __dmul_rn(l, __dmul_rn(A.p[arg], A.tau)));
+    z = __dadd_rn(z, A.f[arg]);
+    const double zr = rint(z);
+    if (fabs(__dsub_rn(z, zr)) < 1e-9) z = zr;
+    if (actions) actions[(size_t)path * T + t - 1] = arg;
+  }
+  revenue[path] = rev;
+  if (s_end) s_end[path] = z;
 }
 
 // rho_t = sum_k pi_t[k] in double
@@ -317,8 +417,8 @@ extern "C" int esdp_iid_actions(const esdp_iid_problem* q, double* p_hat, int32_
 }
 
 extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, const float* pi_hat,
-                              const float* terminal, float* V0, void* policy, uint32_t flags,
-                              void* stream, char* err, int32_t err_len) {
+                              const float* terminal, float* V0, float* V_all, void* policy,
+                              uint32_t flags, void* stream, char* err, int32_t err_len) {
   char buf[256];
   if (!q || !lam_hat || !pi_hat || !V0) return msg(err, err_len, ESDP_EINVAL, "null argument");
   if (q->T < 1 || q->S < 2 || q->R < 1 || q->R > kIidKG * kIidBlock)
@@ -395,7 +495,8 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     for (void* a : allocs) cudaFree(a);
   };
   void *d_pay, *d_dlo, *d_bw, *d_smin, *d_smax, *d_v, *d_ref, *d_flags, *d_status, *d_rho, *d_cta;
-  void *d_lam = nullptr, *d_pi = nullptr, *d_term = nullptr, *d_v0 = nullptr, *d_pol = nullptr;
+  void *d_lam = nullptr, *d_pi = nullptr, *d_term = nullptr, *d_v0 = nullptr, *d_pol = nullptr,
+       *d_vall = nullptr;
   const size_t pol_bytes = (size_t)q->policy_bytes * T * S * R;
   bool ok = alloc(&d_pay, P * 4) && alloc(&d_dlo, P * 4) && alloc(&d_bw, P * 4) &&
             alloc(&d_smin, P * 4) && alloc(&d_smax, P * 4) && alloc(&d_v, (size_t)2 * S * 4) &&
@@ -405,7 +506,8 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
   if (ok && !dev) {
     ok = alloc(&d_lam, (size_t)T * R * 4) && alloc(&d_pi, (size_t)T * R * 4) &&
          alloc(&d_v0, (size_t)S * 4) && (!terminal || alloc(&d_term, (size_t)S * 4)) &&
-         (!q->policy_bytes || alloc(&d_pol, pol_bytes));
+         (!q->policy_bytes || alloc(&d_pol, pol_bytes)) &&
+         (!V_all || alloc(&d_vall, (size_t)(T + 1) * S * 4));
   }
   if (!ok) {
     cleanup();
@@ -461,6 +563,7 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
   ip.pol32 = q->policy_bytes == 4 ? (int*)pol : nullptr;
   ip.pol16 = q->policy_bytes == 2 ? (short*)pol : nullptr;
   ip.v_out = dev ? V0 : (float*)d_v0;
+  ip.v_all = V_all ? (dev ? V_all : (float*)d_vall) : nullptr;
   ip.cta_first = (const int*)d_cta;
   ip.timeout_ns = 5ull * 1000 * 1000 * 1000;
   iid_rho_kernel<<<(T + 127) / 128, 128, 0, st>>>(ip.pi, (double*)d_rho, T, R);
@@ -473,6 +576,8 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     e = cudaMemcpyAsync(V0, d_v0, (size_t)S * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && q->policy_bytes)
       e = cudaMemcpyAsync(policy, d_pol, pol_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && V_all)
+      e = cudaMemcpyAsync(V_all, d_vall, (size_t)(T + 1) * S * 4, cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cleanup();
@@ -484,5 +589,90 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     std::snprintf(buf, sizeof(buf), "device reported status %d", status);
     return msg(err, err_len, status, buf);
   }
+  return ESDP_OK;
+}
+
+namespace {
+
+// the per-action arrays of IidActions on the device
+struct ActionsBuf {
+  double* d = nullptr;
+  IidActions a{};
+};
+
+int make_actions(const esdp_iid_problem& q, ActionsBuf* out, char* err, int32_t err_len) {
+  const std::vector<double> p = action_grid(q);
+  const int P = (int)p.size();
+  const double delta = q.s_max / (double)(q.S - 1);
+  std::vector<double> h(2 * P);
+  for (int a = 0; a < P; ++a) {
+    h[a] = p[a];
+    const double F = p[a] >= 0 ? -p[a] / q.eta : -q.eta * p[a];
+    h[P + a] = F * q.tau / delta;
+  }
+  if (cudaMalloc(&out->d, 2 * P * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return msg(err, err_len, ESDP_ENOMEM, "allocation failed");
+  }
+  if (cudaMemcpy(out->d, h.data(), 2 * P * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(out->d);
+    return msg(err, err_len, ESDP_ECUDA, "copy failed");
+  }
+  out->a.p = out->d;
+  out->a.f = out->d + P;
+  out->a.P = P;
+  out->a.S = q.S;
+  out->a.tau = q.tau;
+  return ESDP_OK;
+}
+
+int check_problem(const esdp_iid_problem* q, char* err, int32_t err_len) {
+  if (!q || q->T < 1 || q->S < 2 || !(q->s_max > 0) || !(q->p_max > 0) || !(q->eta > 0) ||
+      q->eta > 1 || !(q->tau > 0))
+    return msg(err, err_len, ESDP_EINVAL, "invalid problem");
+  return ESDP_OK;
+}
+
+}  // namespace
+
+extern "C" int esdp_iid_bids(const esdp_iid_problem* q, const float* V_all, int32_t t0, int32_t t1,
+                             int32_t* n_bp, int32_t* bp_action, float* bp_price, void* stream,
+                             char* err, int32_t err_len) {
+  int rc = check_problem(q, err, err_len);
+  if (rc) return rc;
+  if (!V_all || !n_bp || !bp_action || !bp_price || t0 < 1 || t1 <= t0 || t1 > q->T + 1)
+    return msg(err, err_len, ESDP_EINVAL, "need V_all, outputs and 1 <= t0 < t1 <= T+1");
+  ActionsBuf ab;
+  if ((rc = make_actions(*q, &ab, err, err_len))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = (long long)(t1 - t0) * q->S;
+  iid_bids_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(ab.a, V_all, t0, t1 - t0, n_bp,
+                                                               bp_action, bp_price);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ab.d);
+  if (e != cudaSuccess) return msg(err, err_len, ESDP_ECUDA, cudaGetErrorString(e));
+  return ESDP_OK;
+}
+
+extern "C" int esdp_iid_clear(const esdp_iid_problem* q, const float* V_all, const float* lam_real,
+                              int32_t n_paths, double s0, double* revenue, double* s_end,
+                              int32_t* actions, void* stream, char* err, int32_t err_len) {
+  int rc = check_problem(q, err, err_len);
+  if (rc) return rc;
+  if (!V_all || !lam_real || !revenue || n_paths < 1)
+    return msg(err, err_len, ESDP_EINVAL, "need V_all, lam_real, revenue and n_paths >= 1");
+  const double z0 = s0 / (q->s_max / (double)(q->S - 1));
+  if (!(z0 >= -1e-9) || z0 > (double)(q->S - 1) + 1e-9)
+    return msg(err, err_len, ESDP_EINVAL, "s0 outside [0, s_max]");
+  ActionsBuf ab;
+  if ((rc = make_actions(*q, &ab, err, err_len))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  iid_clear_kernel<<<(n_paths + 63) / 64, 64, 0, st>>>(ab.a, V_all, q->T, lam_real, n_paths, z0,
+                                                       revenue, s_end, actions);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ab.d);
+  if (e != cudaSuccess) return msg(err, err_len, ESDP_ECUDA, cudaGetErrorString(e));
   return ESDP_OK;
 }

@@ -35,7 +35,8 @@ ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
-           "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_autotune",
+           "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_iid_bids",
+           "esdp_iid_clear", "esdp_autotune",
            "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
 
 
@@ -326,21 +327,23 @@ def iid_actions(prob) -> np.ndarray:
 
 
 def solve_iid(prob, V0=None, policy=None, *, device=False, lam_hat=None, pi_hat=None,
-              terminal=None, policy_bytes=None, stream=None):
+              terminal=None, policy_bytes=None, V_all=None, keep_values=False, stream=None):
     """Algorithm 1 on the GPU (esdp_solve_iid).  Host mode (default): numpy
-    in and out, returns V0 [S] (and the policy [T,S,R] when policy_bytes >
-    0).  Device mode: torch CUDA tensors (or raw device addresses) for
-    lam_hat, pi_hat, terminal, V0 and policy."""
+    in and out, returns V0 [S], then the policy [T,S,R] when policy_bytes > 0
+    and V_all [T+1,S] (V_t of every stage) with keep_values.  Device mode:
+    torch CUDA tensors (or raw device addresses) for lam_hat, pi_hat,
+    terminal, V0, V_all and policy."""
     lib = load_library()
     fn = lib.esdp_solve_iid
-    fn.argtypes = [ctypes.POINTER(IidProblemC)] + [ctypes.c_void_p] * 5 + \
+    fn.argtypes = [ctypes.POINTER(IidProblemC)] + [ctypes.c_void_p] * 6 + \
         [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
     fn.restype = ctypes.c_int
     q = _iid_struct(prob, policy_bytes)
     err = ctypes.create_string_buffer(512)
     if device:
         rc = fn(ctypes.byref(q), _dev_ptr(lam_hat), _dev_ptr(pi_hat), _dev_ptr(terminal),
-                _dev_ptr(V0), _dev_ptr(policy), ESDP_DEVICE_PTRS, _stream(stream), err, len(err))
+                _dev_ptr(V0), _dev_ptr(V_all), _dev_ptr(policy), ESDP_DEVICE_PTRS, _stream(stream),
+                err, len(err))
     else:
         lam = np.ascontiguousarray(prob.lam_hat if lam_hat is None else lam_hat, np.float32)
         pi = np.ascontiguousarray(prob.pi_hat if pi_hat is None else pi_hat, np.float32)
@@ -349,12 +352,70 @@ def solve_iid(prob, V0=None, policy=None, *, device=False, lam_hat=None, pi_hat=
         V0 = np.empty(prob.S, np.float32) if V0 is None else V0
         if q.policy_bytes and policy is None:
             policy = np.empty((prob.T, prob.S, prob.R), np.int16 if q.policy_bytes == 2 else np.int32)
+        if keep_values and V_all is None:
+            V_all = np.empty((prob.T + 1, prob.S), np.float32)
         rc = fn(ctypes.byref(q), lam.ctypes.data, pi.ctypes.data,
                 None if term is None else term.ctypes.data, V0.ctypes.data,
+                None if V_all is None else V_all.ctypes.data,
                 None if policy is None else policy.ctypes.data, 0, _stream(stream), err, len(err))
     if rc != ESDP_OK:
         raise EsdpError(rc, err.value.decode())
-    return (V0, policy) if q.policy_bytes else V0
+    out = (V0,)
+    if q.policy_bytes:
+        out += (policy,)
+    if keep_values and not device:
+        out += (V_all,)
+    return out if len(out) > 1 else V0
+
+
+def iid_bids(prob, V_all, t0: int, t1: int, stream=None):
+    """Convexified bid curves (esdp_iid_bids) of delivery intervals t0..t1-1
+    for every grid SoC, from V_all [T+1,S] on the device (torch).  Returns
+    torch tensors n_bp [n,S], bp_action [n,S,P], bp_price [n,S,P]."""
+    import torch
+    lib = load_library()
+    fn = lib.esdp_iid_bids
+    fn.argtypes = [ctypes.POINTER(IidProblemC), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + \
+        [ctypes.c_void_p] * 4 + [ctypes.c_char_p, ctypes.c_int32]
+    fn.restype = ctypes.c_int
+    q = _iid_struct(prob, 0)
+    P = len(iid_actions(prob))
+    n = t1 - t0
+    dev = V_all.device
+    n_bp = torch.empty((n, prob.S), dtype=torch.int32, device=dev)
+    act = torch.empty((n, prob.S, P), dtype=torch.int32, device=dev)
+    price = torch.empty((n, prob.S, P), dtype=torch.float32, device=dev)
+    err = ctypes.create_string_buffer(512)
+    rc = fn(ctypes.byref(q), _dev_ptr(V_all), t0, t1, _dev_ptr(n_bp), _dev_ptr(act),
+            _dev_ptr(price), _stream(stream), err, len(err))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, err.value.decode())
+    return n_bp, act, price
+
+
+def iid_clear(prob, V_all, lam_real, s0: float, keep_actions: bool = True, stream=None):
+    """Merit-order clearing (esdp_iid_clear) of the price paths lam_real
+    [n_paths,T] (torch, device) from SoC s0 (MWh).  Returns torch tensors
+    revenue [n_paths] (double), s_end [n_paths] (grid steps) and the actions
+    [n_paths,T] (or None)."""
+    import torch
+    lib = load_library()
+    fn = lib.esdp_iid_clear
+    fn.argtypes = [ctypes.POINTER(IidProblemC), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                   ctypes.c_double] + [ctypes.c_void_p] * 4 + [ctypes.c_char_p, ctypes.c_int32]
+    fn.restype = ctypes.c_int
+    q = _iid_struct(prob, 0)
+    n_paths = lam_real.shape[0]
+    dev = lam_real.device
+    rev = torch.empty(n_paths, dtype=torch.float64, device=dev)
+    s_end = torch.empty(n_paths, dtype=torch.float64, device=dev)
+    act = torch.empty((n_paths, prob.T), dtype=torch.int32, device=dev) if keep_actions else None
+    err = ctypes.create_string_buffer(512)
+    rc = fn(ctypes.byref(q), _dev_ptr(V_all), _dev_ptr(lam_real), n_paths, float(s0),
+            _dev_ptr(rev), _dev_ptr(s_end), _dev_ptr(act), _stream(stream), err, len(err))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, err.value.decode())
+    return rev, s_end, act
 
 
 def solve_noalloc(inst, price, trans, cost, terminal, V1, policy=None, stream=None) -> None:

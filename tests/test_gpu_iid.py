@@ -110,3 +110,86 @@ def test_iid_tiles_taller_than_one_pass():
     only 64 rows per pass of the block: rows are taken in two passes."""
     prob = I.iid_problem(10, 6, 10001, 64, 1000.0)
     _check_values(E.solve_iid(prob), _oracle(prob)[0])
+
+
+# ------------------------------------------------ bid curves and clearing
+
+def _device_values(prob):
+    import torch
+    lam = torch.from_numpy(prob.lam_hat).cuda()
+    pi = torch.from_numpy(prob.pi_hat).cuda()
+    V0 = torch.empty(prob.S, device="cuda")
+    V_all = torch.empty((prob.T + 1, prob.S), device="cuda")
+    E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi, V_all=V_all)
+    torch.cuda.synchronize()
+    return V0, V_all
+
+
+def test_iid_kept_values_match_algorithm1():
+    prob = I.iid_problem(12, 20, 81, 9, 4.0, terminal=True)
+    V0, pol, V_all = E.solve_iid(prob, policy_bytes=4, keep_values=True)
+    np.testing.assert_array_equal(V_all[0], V0)
+    ref = _oracle(prob)
+    scale = max(np.abs(ref).max(), 1.0)
+    assert np.abs(V_all.astype(np.float64) - ref).max() / scale <= VTOL
+
+
+def test_iid_bid_curves_bit_exact():
+    """Vertices identical to the oracle's envelope on the GPU's own values
+    (same double predicate), prices to float32, monotone bids."""
+    prob = I.iid_problem(13, 10, 61, 8, 3.0, neg_prob=0.3)
+    _, V_all = _device_values(prob)
+    n_bp, act, price = E.iid_bids(prob, V_all, 1, prob.T + 1)
+    n_bp, act, price = n_bp.cpu().numpy(), act.cpu().numpy(), price.cpu().numpy()
+    V = V_all.cpu().numpy()
+    non_concave = 0
+    for t in range(1, prob.T + 1):
+        for s in range(prob.S):
+            idx, pr = O.paper_bids(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau, V[t], s)
+            n = n_bp[t - 1, s]
+            assert n == len(idx)
+            np.testing.assert_array_equal(act[t - 1, s, :n], idx)
+            np.testing.assert_allclose(price[t - 1, s, :n - 1], pr, rtol=1e-6, atol=1e-6)
+            assert np.all(np.diff(price[t - 1, s, :n - 1]) >= 0)
+            p, f = O._shifts(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau)
+            feas = sum(1 for a in range(len(p)) if -1e-9 <= s + f[a] <= prob.S - 1 + 1e-9)
+            non_concave += n < feas
+    assert non_concave > 0   # negative prices make some U non-concave: convexification acts
+
+
+def test_iid_clearing_matches_oracle():
+    import torch
+    prob = I.iid_problem(14, 24, 41, 6, 4.0, neg_prob=0.2)
+    _, V_all = _device_values(prob)
+    rng = np.random.default_rng(5)
+    lam = (prob.lam_hat.mean(axis=1)[None, :] * rng.lognormal(0.0, 0.4, size=(16, prob.T))
+           - 5.0).astype(np.float32)
+    rev, s_end, act = E.iid_clear(prob, V_all, torch.from_numpy(lam).cuda(), 2.0)
+    rev, s_end, act = rev.cpu().numpy(), s_end.cpu().numpy(), act.cpu().numpy()
+    V = V_all.cpu().numpy()
+    for i in range(lam.shape[0]):
+        r, z, a = O.paper_clear(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau, V, lam[i], 2.0)
+        np.testing.assert_array_equal(act[i], a)
+        assert rev[i] == pytest.approx(r, rel=1e-12, abs=1e-9)
+        assert s_end[i] == pytest.approx(z, abs=1e-9)
+
+
+def test_iid_clearing_monte_carlo_reproduces_value():
+    """Price paths drawn from the model's own samples (eta = 1: every action
+    on the grid): the mean cleared revenue is V_0(s0) within 3 standard
+    errors."""
+    import torch
+    prob = I.iid_problem(15, 48, 81, 12, 4.0, eta=1.0, weights="dirichlet")
+    V0, V_all = _device_values(prob)
+    rng = np.random.default_rng(9)
+    n = 20000
+    pi = prob.pi_hat.astype(np.float64)
+    cum = np.cumsum(pi / pi.sum(axis=1, keepdims=True), axis=1)
+    u = rng.random((n, prob.T))
+    k = (u[:, :, None] > cum[None, :, :]).sum(axis=2).clip(0, prob.R - 1)
+    lam = prob.lam_hat[np.arange(prob.T)[None, :], k].astype(np.float32)
+    rev, _, _ = E.iid_clear(prob, V_all, torch.from_numpy(lam).cuda(), 2.0, keep_actions=False)
+    rev = rev.cpu().numpy()
+    se = rev.std(ddof=1) / math.sqrt(n)
+    target = float(V0.cpu().numpy()[int(round(2.0 / prob.delta))])
+    assert abs(rev.mean() - target) <= 3 * se, (rev.mean(), target, se)

@@ -600,3 +600,65 @@ def test_hull_bruteforce(seed):
         assert env[i] == pytest.approx(best, rel=1e-12, abs=1e-12)
     s = O.hull_slopes(y, h, 1.0)
     assert np.all(np.diff(s) < 0)        # monotone bid prices (eq. 11)
+
+
+
+# ----------------------------------------------- bid curves and clearing (Sec. II-C, V)
+
+def test_paper_bids_envelope_by_brute_force():
+    """The bid vertices are exactly the points above every chord (the
+    envelope definition) and the prices are monotone non-decreasing."""
+    rng = np.random.default_rng(11)
+    S, s_max, p_max, eta, tau = 41, 4.0, 1.0, math.sqrt(0.85), 1.0
+    for trial in range(6):
+        v = np.cumsum(rng.normal(2.0, 3.0, size=S)).astype(np.float32)  # non-concave
+        s = int(rng.integers(0, S))
+        idx, prices = O.paper_bids(S, s_max, p_max, eta, tau, v, s)
+        p, f = O._shifts(S, s_max, p_max, eta, tau)
+        pts = [(a, p[a], O._v_at(v, s + f[a])) for a in range(len(p))
+               if -1e-9 <= s + f[a] <= S - 1 + 1e-9]
+        xs = [Fraction(x) for _, x, _ in pts]
+        ys = [Fraction(y) for _, _, y in pts]
+        brute = [pts[0][0]]
+        for i in range(1, len(pts) - 1):
+            if all(ys[i] > ys[j] + (ys[l] - ys[j]) * (xs[i] - xs[j]) / (xs[l] - xs[j])
+                   for j in range(i) for l in range(i + 1, len(pts))):
+                brute.append(pts[i][0])
+        brute.append(pts[-1][0])
+        assert idx == brute
+        assert all(b >= a for a, b in zip(prices, prices[1:]))
+
+
+def test_paper_bids_concave_value_keeps_every_action():
+    """V concave and increasing in SoC (Sec. II-C): U(p; s) is concave in p,
+    every feasible action is on the envelope (up to collinear runs) and the
+    bid at zero power lies between the discharge and charge marginal values."""
+    S, s_max, p_max, eta, tau = 81, 4.0, 1.0, math.sqrt(0.85), 1.0
+    x = np.arange(S) * (s_max / (S - 1))
+    v = (50.0 * x - 4.0 * x ** 2).astype(np.float32)
+    idx, prices = O.paper_bids(S, s_max, p_max, eta, tau, v, 40)
+    p, f = O._shifts(S, s_max, p_max, eta, tau)
+    feas = [a for a in range(len(p)) if -1e-9 <= 40 + f[a] <= S - 1 + 1e-9]
+    assert len(idx) >= len(feas) - 2
+    assert all(b >= a for a, b in zip(prices, prices[1:]))
+
+
+def test_paper_clear_reproduces_dp_value_in_expectation():
+    """Paths drawn from the model's own price samples: the clearing policy
+    is the DP's maximiser, so the mean revenue is V_0(s0) (zero terminal,
+    eta = 1 so that every action stays on the grid) within 3 standard errors."""
+    prob = I.iid_problem(21, 8, 21, 5, 2.0, eta=1.0)
+    V = O.paper_alg1(prob.s_max, prob.delta, prob.p_max, prob.eta, prob.lam_hat, prob.pi_hat)
+    rng = np.random.default_rng(3)
+    n = 4000
+    s0 = 1.0
+    revs = []
+    for _ in range(n):
+        k = [rng.choice(prob.R, p=prob.pi_hat[t].astype(np.float64) / prob.pi_hat[t].sum())
+             for t in range(prob.T)]
+        lam = prob.lam_hat[np.arange(prob.T), k]
+        revs.append(O.paper_clear(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau, V, lam, s0)[0])
+    revs = np.array(revs)
+    se = revs.std(ddof=1) / math.sqrt(n)
+    target = V[0][int(round(s0 / prob.delta))]
+    assert abs(revs.mean() - target) <= 3 * se + 1e-9, (revs.mean(), target, se)
