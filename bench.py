@@ -530,8 +530,40 @@ def bench_table3(torch, E, I, stream, flush, args, n_sm, f_max):
     return out
 
 
+def bench_bids_clearing(torch, E, I, stream, flush, args, n_sm, f_max):
+    """The paper's bid-curve and clearing steps on the Table III 20 h / S = 2001
+    / P = 203 shape: values of every stage kept, convexified bid curves of one
+    day (24 delivery intervals x 2001 SoC states), and merit-order clearing of
+    1024 realised price paths over the full year (8784 stages each)."""
+    prob = I.table3_problem(4)
+    lam = torch.from_numpy(prob.lam_hat).cuda()
+    pi = torch.from_numpy(prob.pi_hat).cuda()
+    V0 = torch.empty(prob.S, device="cuda")
+    V_all = torch.empty((prob.T + 1, prob.S), device="cuda")
+    rng = np.random.default_rng(17)
+    paths = torch.from_numpy((prob.lam_hat[np.arange(prob.T)[None, :],
+                                           rng.integers(0, prob.R, size=(1024, prob.T))])
+                             .astype(np.float32)).cuda()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+    t_solve = timed(lambda: E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi, V_all=V_all))
+    t_bids = timed(lambda: E.iid_bids(prob, V_all, 1, 25))
+    t_clear = timed(lambda: E.iid_clear(prob, V_all, paths, 10.0, keep_actions=False))
+    rev = E.iid_clear(prob, V_all, paths, 10.0, keep_actions=False)[0]
+    return {"case": prob.name, "solve_keep_values_s": t_solve, "bid_curves_24x2001_s": t_bids,
+            "clearing_1024_paths_s": t_clear,
+            "clearing_path_stages_per_s": 1024 * prob.T / t_clear,
+            "mean_revenue_per_path": float(rev.mean()), "V0_at_s0": float(V0[1000])}
+
+
 EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
-          "paper_table3": bench_table3}
+          "paper_table3": bench_table3, "paper_bids_clearing": bench_bids_clearing}
 
 
 def run_profile_case(name):

@@ -336,19 +336,22 @@ __global__ void iid_bids_kernel(const IidActions A, const float* v_all, int t0, 
 // actions (the vertex of the convexified bid curve where the bid price
 // crosses lam_t; the first such action on ties), the SoC moves by F(p) tau
 // (off the grid at the end points: V_t interpolated there) and the revenue
-// lam_t p tau accrues.  One thread per price path.
+// lam_t p tau accrues.  One warp per price path: the lanes take the actions
+// in turn and the warp reduces (larger value, on equal values the smaller
+// action index).
 __global__ void iid_clear_kernel(const IidActions A, const float* v_all, int T, const float* lam,
                                  int n_paths, double s0, double* revenue, double* s_end,
                                  int* actions) {
-  const int path = blockIdx.x * blockDim.x + threadIdx.x;
-  if (path >= n_paths) return;
+  const int lane = threadIdx.x & 31;
+  const int path = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (path >= n_paths) return;  // whole warps leave together
   double z = s0, rev = 0.0;
   for (int t = 1; t <= T; ++t) {
     const float* v = v_all + (size_t)t * A.S;
     const double l = (double)lam[(size_t)path * T + t - 1];
     double best = -INFINITY;
-    int arg = -1;
-    for (int a = 0; a < A.P; ++a) {
+    int arg = 0x7fffffff;
+    for (int a = lane; a < A.P; a += 32) {
       const double zn = __dadd_rn(z, A.f[a]);
       if (!feasible(zn, A.S)) continue;
       const double val = __dadd_rn(__dmul_rn(l, __dmul_rn(A.p[a], A.tau)), v_at(v, A.S, zn));
@@ -357,15 +360,26 @@ __global__ void iid_clear_kernel(const IidActions A, const float* v_all, int T, 
         arg = a;
       }
     }
-    if (arg < 0) arg = 0;  // not reached: idle is always feasible
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (ob > best || (ob == best && oa < arg)) {
+        best = ob;
+        arg = oa;
+      }
+    }
+    if (arg == 0x7fffffff) arg = 0;  // not reached: idle is always feasible
     rev = __dadd_rn(rev, __dmul_rn(l, __dmul_rn(A.p[arg], A.tau)));
     z = __dadd_rn(z, A.f[arg]);
     const double zr = rint(z);
     if (fabs(__dsub_rn(z, zr)) < 1e-9) z = zr;
-    if (actions) actions[(size_t)path * T + t - 1] = arg;
+    if (actions && lane == 0) actions[(size_t)path * T + t - 1] = arg;
   }
-  revenue[path] = rev;
-  if (s_end) s_end[path] = z;
+  if (lane == 0) {
+    revenue[path] = rev;
+    if (s_end) s_end[path] = z;
+  }
 }
 
 // rho_t = sum_k pi_t[k] in double
@@ -668,8 +682,8 @@ extern "C" int esdp_iid_clear(const esdp_iid_problem* q, const float* V_all, con
   ActionsBuf ab;
   if ((rc = make_actions(*q, &ab, err, err_len))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  iid_clear_kernel<<<(n_paths + 63) / 64, 64, 0, st>>>(ab.a, V_all, q->T, lam_real, n_paths, z0,
-                                                       revenue, s_end, actions);
+  iid_clear_kernel<<<(unsigned)(((long long)n_paths * 32 + 255) / 256), 256, 0, st>>>(
+      ab.a, V_all, q->T, lam_real, n_paths, z0, revenue, s_end, actions);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(ab.d);
