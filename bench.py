@@ -243,6 +243,7 @@ def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
 
 def run_esdp(args, rank, world):
     import torch
+    from paper_2511_15629_b300 import dist as D
     from paper_2511_15629_b300 import esdp as E
     from paper_2511_15629_b300 import instances as I
     dev = torch.cuda.current_device()
@@ -293,12 +294,8 @@ def run_esdp(args, rank, world):
                                               flush, marks=2)
     torch.cuda.synchronize()
     assert s.status(stream=stream) == 0, "device status after the timed steps"
-    t_local = torch.tensor([total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    total = float(t_local.item())
-    value = inst.evals * args.steps * world / total
+    total = D.job_seconds(total, torch, device="cuda")  # max over ranks
+    value = D.aggregate_rate(inst.evals * args.steps, world, total)
     sweep_evals_s = inst.evals * args.steps / t_sweep
     peak = alu_peak_evals(n_sm, f_max)
     clocks = clk.summary()
@@ -400,7 +397,12 @@ def bench_config3(torch, E, I, stream, flush, args, n_sm, f_max):
 def bench_config4(torch, E, I, stream, flush, args, n_sm, f_max):
     """256 heterogeneous assets in one graph-captured persistent launch,
     against 256 sequential single-asset solves."""
+    from paper_2511_15629_b300 import dist as D
     assets = I.config4(256)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:  # the portfolio shards: this rank's assets (LPT on the evaluations)
+        mine = D.shard_by_cost([a.evals for a in assets], world)[int(os.environ.get("RANK", "0"))]
+        assets = [assets[i] for i in mine]
     evals = sum(a.evals for a in assets)
     cat = E.concat_inputs(assets)
     d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
