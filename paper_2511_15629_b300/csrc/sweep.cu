@@ -828,19 +828,10 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     // winning chunk that reproduces the max (the same two round-to-nearest
     // operations as the packed evaluation); V'_t = max + c_{t+1} rho_t[k] - c_t
     if (active) {
-#pragma unroll 2
-      for (int e = part; e < 2 * R; e += G) {
-        const int j = e >> 1, h = e & 1;
-        float bj = 0.f;
-        int c = -1;
-#pragma unroll
-        for (int jj = 0; jj < R; ++jj)
-          if (jj == j) {
-            bj = h ? best[jj].y : best[jj].x;
-            c = h ? by[jj] : bx[jj];
-          }
+      // one entry: its max bj and winning chunk c
+      auto recover = [&](int j, int h, float bj, int c) {
         const int row = b * R + j, k = k0 + h;
-        if (k >= K || row >= Wt) continue;
+        if (k >= K || row >= Wt) return;
         const float lk = h ? lam.y : lam.x;
         int arg = -1;
         if (c >= 0) {
@@ -865,6 +856,35 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
         }
         put_v(sm.Vs, sm.Ah, sm.Al, as, Wt, m, row, k, bj + sm.delta[k]);
         Xi[(m * W + row) * K + k] = arg;
+      };
+      if (G == 2) {
+        // lane `part` takes state k0 + part of every row
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          recover(j, part, part ? best[j].y : best[j].x, part ? by[j] : bx[j]);
+      } else if (G == 4) {
+        // lane `part` takes state k0 + (part & 1) of the rows j = part/2 + 2i
+        const int h = part & 1, jo = part >> 1;
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+          const float2 bb = jo ? best[2 * i + 1] : best[2 * i];
+          const int cx = jo ? bx[2 * i + 1] : bx[2 * i], cy = jo ? by[2 * i + 1] : by[2 * i];
+          recover(2 * i + jo, h, h ? bb.y : bb.x, h ? cy : cx);
+        }
+      } else {
+#pragma unroll 2
+        for (int e = part; e < 2 * R; e += G) {
+          const int j = e >> 1, h = e & 1;
+          float bj = 0.f;
+          int c = -1;
+#pragma unroll
+          for (int jj = 0; jj < R; ++jj)
+            if (jj == j) {
+              bj = h ? best[jj].y : best[jj].x;
+              c = h ? by[jj] : bx[jj];
+            }
+          recover(j, h, bj, c);
+        }
       }
     }
   }
