@@ -193,3 +193,22 @@ def test_iid_clearing_monte_carlo_reproduces_value():
     se = rev.std(ddof=1) / math.sqrt(n)
     target = float(V0.cpu().numpy()[int(round(2.0 / prob.delta))])
     assert abs(rev.mean() - target) <= 3 * se, (rev.mean(), target, se)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(S=2, R=1, hours=1.0),                         # two SoC points, one sample
+    dict(S=11, R=3, hours=1.0, p_max=0.03),            # p_max below one SoC step: P = 3
+    dict(S=21, R=4, hours=0.5, p_max=2.0),             # end points beyond the whole range
+    dict(S=301, R=9, hours=30.0, p_max=5.0),           # wide action grid, halo over many tiles
+])
+def test_iid_edge_shapes(kw):
+    hours = kw.pop("hours")
+    p_max = kw.pop("p_max", 1.0)
+    prob = I.iid_problem(30, 12, kw["S"], kw["R"], hours, p_max=p_max)
+    P = len(E.iid_actions(prob))
+    assert P >= 3
+    V0, pol = E.solve_iid(prob, policy_bytes=4)
+    V, ref_pol, gap = _oracle(prob, keep_policy=True)
+    scale = _check_values(V0, V[0])
+    decided = gap >= GAPTOL * scale
+    assert not ((pol.astype(np.int64) != ref_pol) & decided).any()
