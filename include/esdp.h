@@ -70,7 +70,7 @@ extern "C" {
 typedef struct esdp_ctx esdp_ctx;
 
 typedef struct {
-  int32_t T, N, K, A;     /* stages, SoC points, price states, actions */
+  int32_t T, N, K, A;     /* stages, SoC points (2..2^24), price states, actions */
   int32_t D_dis, D_chg;   /* action band: shifts -D_dis..+D_chg, A = D_dis+D_chg+1 */
   int32_t n_modes;        /* 1, or 2 = charge->discharge switch-cost flag */
   int32_t policy_bytes;   /* 4 (int32), 2 (int16) or 0 (policy not kept) */

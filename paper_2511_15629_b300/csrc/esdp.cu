@@ -146,6 +146,8 @@ int round_up(int x, int r) { return (x + r - 1) / r * r; }
 int validate_asset(esdp_ctx* c, const esdp_asset& a, int i) {
   if (a.T < 1 || a.N < 2 || a.K < 1 || a.A < 1)
     return fail(c, ESDP_EINVAL, "asset %d: T, K, A must be >= 1 and N >= 2", i);
+  if (a.N > (1 << 24))  // SoC indices are exact in float32 (bid-curve predicate)
+    return fail(c, ESDP_EINVAL, "asset %d: N must be at most 2^24", i);
   if (a.D_dis < 0 || a.D_chg < 0 || a.D_dis + a.D_chg + 1 != a.A)
     return fail(c, ESDP_EINVAL, "asset %d: A must equal D_dis + D_chg + 1", i);
   if (a.D_dis > a.N - 1 || a.D_chg > a.N - 1)

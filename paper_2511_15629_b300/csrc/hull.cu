@@ -4,20 +4,20 @@
 // the monotone marginal values of stored energy from which the price-quantity
 // bids are read.
 //
-// A block handles 32 envelopes (consecutive lanes take consecutive price
-// states, so every load is one coalesced row of EV) with kSeg warps: warp q
-// first builds the envelope of the q-th segment of the SoC grid of all 32,
-// then warp 0 merges the segment envelopes.  Every strict vertex of the whole
-// envelope is a strict vertex of its segment's envelope, so the chain over
-// the concatenated segment vertices yields exactly the envelope of all points.
+// One warp per envelope: the lanes build the hulls of 32 consecutive parts of
+// the SoC grid and join them pairwise by upper bridges (details at the
+// kernel).  The joined hull of two adjacent strict hulls is a prefix of the
+// left one, the bridge, and a suffix of the right one, so every strict vertex
+// of the whole envelope survives from its part's hull.
 //
 // A middle point j between i and l is dropped when
 //     (y_j - y_i) * (l - i) - (y_l - y_i) * (j - i)  <= 0.
 // Its exact sign is taken: in float32 when the value clears a rigorous
-// rounding bound, otherwise in 128-bit integers on a common binary grid of the
-// three values, and, for exponent spreads beyond 38 bits, by the double
-// expression, which is exact up to its last subtraction (whose rounding
-// cannot change the sign).  The vertex set is therefore a deterministic
+// rounding bound, otherwise by error-free float32 transformations (TwoSum,
+// FMA residuals) where they settle it, else in 128-bit integers on a common
+// binary grid of the three values, and, for exponent spreads beyond 38 bits,
+// by the double expression, which is exact up to its last subtraction (whose
+// rounding cannot change the sign).  The vertex set is therefore a deterministic
 // function of the float32 EV values.
 #include <cuda_runtime.h>
 
@@ -26,8 +26,6 @@
 namespace esdp {
 namespace {
 
-constexpr int kSeg = 8;    // segments (warps) per block
-constexpr int kWin = 16;   // stack entries cached per thread in shared memory
 
 // float32 value as mantissa * 2^(e - 150) with a signed integer mantissa
 __device__ __forceinline__ void decompose(float v, long long& m, int& e) {
@@ -62,146 +60,310 @@ __device__ bool below_exact(float yi, float yj, float yl, int L, int J) {
   return __dsub_rn(dl, dr) <= 0.0;
 }
 
-// true if point j lies on or below the chord from i to l
-__device__ __forceinline__ bool below_chord(float yi, float yj, float yl, int i, int j, int l) {
-  const float L = (float)(l - i), J = (float)(j - i);  // exact: grid sizes < 2^24
+// rounding error of s = RN(a + b): a + b = s + err exactly (Knuth's TwoSum)
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  return __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Exact sign of the cross product by error-free float32 transformations, for
+// the near-collinear triples the rounded test leaves open.  With
+// a = RN(yj - yi), b = RN(yl - yi) exact (TwoSum errors zero), the products
+// split exactly as a L = lhs + e1, b J = rhs + e2 (FMA residuals, exact away
+// from underflow), and lhs - rhs = d exactly (TwoSum error zero), so the cross
+// product is d + e1 - e2.  Its sign is that of e1 - e2 when d = 0 and that of
+// d when |d| > 2 max(|e1|, |e2|).  Returns 1 (on or below), 0 (above) or -1
+// (not decided here).
+__device__ __forceinline__ int below_near(float yi, float yj, float yl, float L, float J) {
+  const float a = __fsub_rn(yj, yi), b = __fsub_rn(yl, yi);
+  if (two_sum_err(yj, -yi, a) != 0.f || two_sum_err(yl, -yi, b) != 0.f) return -1;
+  const float lhs = __fmul_rn(a, L), rhs = __fmul_rn(b, J);
+  // residuals are exact unless the products are near the underflow range
+  if ((lhs != 0.f && fabsf(lhs) < 1e-28f) || (rhs != 0.f && fabsf(rhs) < 1e-28f)) return -1;
+  const float e1 = __fmaf_rn(a, L, -lhs), e2 = __fmaf_rn(b, J, -rhs);
+  const float d = __fsub_rn(lhs, rhs);
+  if (two_sum_err(lhs, -rhs, d) != 0.f) return -1;
+  if (d == 0.f) return e1 <= e2;
+  if (fabsf(d) > 2.f * fmaxf(fabsf(e1), fabsf(e2))) return d < 0.f;
+  return -1;
+}
+
+// true if point j lies on or below the chord from i to l (SoC indices as
+// float32, exact below 2^24, and so are their differences)
+__device__ __forceinline__ bool below_chord(float yi, float yj, float yl, float xi, float xj,
+                                            float xl) {
+  const float L = __fsub_rn(xl, xi), J = __fsub_rn(xj, xi);
   const float lhs = __fmul_rn(__fsub_rn(yj, yi), L);
   const float rhs = __fmul_rn(__fsub_rn(yl, yi), J);
   const float cross = __fsub_rn(lhs, rhs);
   // each side carries at most two roundings, the difference one more:
   // |cross - exact| <= (2u + u^2)(|lhs| + |rhs|)(1 + u) + u |cross|, u = 2^-24
   // (taken as 5u, plus an absolute floor so that subnormal ranges always go
-  // to the exact route)
+  // to the exact routes)
   const float bound = 3.0e-7f * (fabsf(lhs) + fabsf(rhs)) + 1e-30f;
   if (cross > bound) return false;
   if (cross < -bound) return true;
-  return below_exact(yi, yj, yl, l - i, j - i);
+  const int near = below_near(yi, yj, yl, L, J);
+  if (near >= 0) return near != 0;
+  return below_exact(yi, yj, yl, (int)L, (int)J);
 }
 
-// Monotone chain over a stream of points (index, value) in increasing index
-// order.  The stack lives in global memory at `stack`; its top kWin entries
-// are mirrored in shared memory (slot-major, conflict-free) and the top two in
-// registers.
-struct Chain {
-  int* stack;
-  int* s_idx;    // this thread's column of the shared window
-  float* s_y;
-  const float* y;
+// One warp per envelope.  Lane l takes the points [l c, (l+1) c) of the SoC
+// grid (c = ceil(N/32) rounded up to odd, so that the lanes' equal steps fall
+// in distinct shared-memory banks) and builds their strict upper hull with the
+// monotone chain.  Five levels then join adjacent groups of lanes: the leader
+// of each pair finds the upper bridge of the left and the right hull by the
+// tangent walk (drop the left end point while it lies on or below the chord
+// from its predecessor to the right end point, drop the right end point while
+// it lies on or below the chord from the left end point to its successor,
+// until neither moves), and only trims the kept range of each lane's stack
+// (no copying): the joined hull is the left hull up to the bridge and the
+// right hull from it.  The surviving ranges are read out in order by a prefix
+// sum and a binary search over the lanes, so that the index and slope rows
+// are written coalesced.  With the exact orientation sign the vertex set is
+// the unique set of strict vertices, the same as one monotone chain over all
+// points.
+//
+// kStaged: a block of nw warps first copies the columns of its nw envelopes
+// into shared memory (cp.async; consecutive threads read consecutive price
+// states of one SoC row); each lane's stack then keeps the SoC index (as an
+// exact float) and, in place of the column, the value of its vertices, so a
+// pop or a walk step needs no dependent lookup.  N * 8 bytes per warp.  For
+// grids too long for that, the values are read in place and the slope row
+// holds the stacks' indices.
+constexpr int kHullWarps = 8;
+constexpr int kHullSmemBudget = 96 * 1024;  // dynamic shared memory per block
+
+template <bool kStaged>
+struct HullView {
+  const float* y;   // in place: the envelope's column, stride K
+  float* sv;        // staged: the column, overwritten by the stacks' values
+  float* st;        // stacks' SoC indices (lane l from position l*c)
   int K;
-  int nh = 0, win = 0;
-  int i_idx = 0, j_idx = 0;
-  float yi = 0.f, yj = 0.f;
-
-  __device__ __forceinline__ int slot(int pos) const {
-    return (pos & (kWin - 1)) * (32 * kSeg);
+  int* lo;          // [32] kept range [lo, hi) of each lane's stack
+  int* hi;
+  // value of SoC point l before the local hulls
+  __device__ __forceinline__ float point(int l) const {
+    if constexpr (kStaged)
+      return sv[l];
+    else
+      return __ldg(y + (size_t)l * K);
   }
-
-  __device__ __forceinline__ void push(int l, float yl) {
-    while (nh >= 2 && below_chord(yi, yj, yl, i_idx, j_idx, l)) {
-      --nh;  // j is on or below the chord (i, l)
-      win = max(win - 1, 0);  // positions [nh - win, nh) are cached
-      j_idx = i_idx;
-      yj = yi;
-      if (nh >= 2) {
-        if (win >= 2) {
-          i_idx = s_idx[slot(nh - 2)];
-          yi = s_y[slot(nh - 2)];
-        } else {
-          i_idx = stack[nh - 2];
-          yi = __ldg(y + (size_t)i_idx * K);
-        }
+  // value of the stack entry at position pos
+  __device__ __forceinline__ float val(int pos) const {
+    if constexpr (kStaged)
+      return sv[pos];
+    else
+      return __ldg(y + (size_t)(int)st[pos] * K);
+  }
+  // previous kept vertex of (l, i) within lanes >= lmin, or l = -1
+  __device__ __forceinline__ void prev(int& l, int& i, int lmin) const {
+    if (i > lo[l]) {
+      --i;
+      return;
+    }
+    for (int q = l - 1; q >= lmin; --q)
+      if (hi[q] > lo[q]) {
+        l = q;
+        i = hi[q] - 1;
+        return;
       }
+    l = -1;
+  }
+  // next kept vertex of (l, i) within lanes < lend, or l = -1
+  __device__ __forceinline__ void next(int& l, int& i, int lend) const {
+    if (i + 1 < hi[l]) {
+      ++i;
+      return;
     }
-    s_idx[slot(nh)] = l;
-    s_y[slot(nh)] = yl;
-    stack[nh] = l;
-    ++nh;
-    win = min(win + 1, kWin);
-    if (nh == 1) {
-      j_idx = l;
-      yj = yl;
-    } else {
-      i_idx = j_idx;
-      yi = yj;
-      j_idx = l;
-      yj = yl;
-    }
+    for (int q = l + 1; q < lend; ++q)
+      if (hi[q] > lo[q]) {
+        l = q;
+        i = lo[q];
+        return;
+      }
+    l = -1;
   }
 };
 
-__global__ void __launch_bounds__(32 * kSeg) hull_kernel(const HullParams p) {
-  __shared__ int s_idx[kWin * 32 * kSeg];
-  __shared__ float s_y[kWin * 32 * kSeg];
-  __shared__ int s_cnt[kSeg][32];
-  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+// slope between two vertices, $ per MWh of stored energy
+__device__ __forceinline__ float hull_slope(float xa, float ya, float xb, float yb, double delta) {
+  return (float)(__ddiv_rn(__dsub_rn((double)yb, (double)ya),
+                           __dmul_rn((double)__fsub_rn(xb, xa), delta)));
+}
+
+// blockDim.x = 32 << lg_nw
+template <bool kStaged>
+__global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams p, int lg_nw) {
+  extern __shared__ float hull_smem[];  // staged: [nw][N] values, then [nw][N] indices
+  __shared__ int s_lo[kHullWarps][32], s_hi[kHullWarps][32], s_pre[kHullWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = 1 << lg_nw;
   const int n_h = p.n_t * p.M * p.K;
-  const int h = blockIdx.x * 32 + lane;
-  const bool valid = h < n_h;
   const int K = p.K, N = p.N;
-  const int k = valid ? h % K : 0;
-  const int tm = valid ? h / K : 0;  // stage-major, then mode
-  const float* y = p.ev + (size_t)tm * N * K + k;
-  int* row = p.idx + (size_t)(valid ? h : 0) * N;
-  const int seg = (N + kSeg - 1) / kSeg;
-
-  // 1. envelope of segment q of the hull, stacked in place in its own range
-  if (valid) {
-    const int l0 = q * seg, l1 = min(N, l0 + seg);
-    Chain ch;
-    ch.stack = row + l0;
-    ch.s_idx = s_idx + threadIdx.x;
-    ch.s_y = s_y + threadIdx.x;
-    ch.y = y;
-    ch.K = K;
-    constexpr int kAhead = 8;
-    float cur[kAhead], nxt[kAhead];
-#pragma unroll
-    for (int u = 0; u < kAhead; ++u) cur[u] = l0 + u < l1 ? __ldg(y + (size_t)(l0 + u) * K) : 0.f;
-    for (int b = l0; b < l1; b += kAhead) {
-#pragma unroll
-      for (int u = 0; u < kAhead; ++u)
-        nxt[u] = b + kAhead + u < l1 ? __ldg(y + (size_t)(b + kAhead + u) * K) : 0.f;
-#pragma unroll
-      for (int u = 0; u < kAhead; ++u)
-        if (b + u < l1) ch.push(b + u, cur[u]);
-#pragma unroll
-      for (int u = 0; u < kAhead; ++u) cur[u] = nxt[u];
+  const int h0 = blockIdx.x * nw;
+  if constexpr (kStaged) {
+    // thread -> envelope h0 + (tid mod nw), SoC rows tid/nw, tid/nw + 32, ...
+    const int ww = threadIdx.x & (nw - 1), hh = h0 + ww;
+    if (hh < n_h) {
+      const float* col = p.ev + (size_t)(hh / K) * N * K + hh % K;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(hull_smem + ww * N);
+      for (int l = threadIdx.x >> lg_nw; l < N; l += 32)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst + 4u * (unsigned)l),
+                     "l"(col + (size_t)l * K)
+                     : "memory");
     }
-    s_cnt[q][lane] = l0 < l1 ? ch.nh : 0;
-  } else {
-    s_cnt[q][lane] = 0;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
   }
-  __syncthreads();
+  const int h = h0 + w;
+  if (h >= n_h) return;  // whole warps, after the block's only barrier
+  const int k = h % K, tm = h / K;  // stage-major, then mode
+  int* row = p.idx + (size_t)h * N;
+  float* sl = p.slope + (size_t)h * N;
+  HullView<kStaged> v;
+  v.K = K;
+  v.lo = s_lo[w];
+  v.hi = s_hi[w];
+  if constexpr (kStaged) {
+    v.y = nullptr;
+    v.sv = hull_smem + w * N;
+    v.st = hull_smem + (nw + w) * N;
+  } else {
+    v.y = p.ev + (size_t)tm * N * K + k;
+    v.sv = nullptr;
+    v.st = sl;  // scratch until the slopes
+  }
+  const int c = ((N + 31) / 32) | 1;
 
-  // 2. merge: the chain over the segment vertices in order, written in place
-  //    (the output position never passes the entries still to be read)
-  if (q == 0 && valid) {
-    Chain ch;
-    ch.stack = row;
-    ch.s_idx = s_idx + threadIdx.x;
-    ch.s_y = s_y + threadIdx.x;
-    ch.y = y;
-    ch.K = K;
-    for (int s = 0; s < kSeg; ++s) {
-      const int n = s_cnt[s][lane];
-      for (int v = 0; v < n; ++v) {
-        const int l = row[s * seg + v];
-        ch.push(l, __ldg(y + (size_t)l * K));
+  // 1. local hull of the lane's points
+  const int l0 = min(N, lane * c), l1 = min(N, l0 + c);
+  int nh = 0;
+  float xi = 0.f, xj = 0.f, yi = 0.f, yj = 0.f;
+  float xl = (float)l0;
+  for (int l = l0; l < l1; ++l, xl = __fadd_rn(xl, 1.f)) {
+    const float yl = v.point(l);
+    while (nh >= 2 && below_chord(yi, yj, yl, xi, xj, xl)) {
+      --nh;
+      xj = xi;
+      yj = yi;
+      if (nh >= 2) {
+        xi = v.st[l0 + nh - 2];
+        yi = v.val(l0 + nh - 2);
       }
     }
-    p.n_bp[h] = ch.nh;
-    s_cnt[0][lane] = ch.nh;
+    v.st[l0 + nh] = xl;
+    if constexpr (kStaged) v.sv[l0 + nh] = yl;  // position <= l: already read
+    ++nh;
+    if (nh == 1) {
+      xj = xl;
+      yj = yl;
+    } else {
+      xi = xj;
+      yi = yj;
+      xj = xl;
+      yj = yl;
+    }
   }
-  __syncthreads();
+  v.lo[lane] = 0;
+  v.hi[lane] = nh;
+  __syncwarp();
 
-  // 3. slopes between consecutive vertices, $ per MWh of stored energy
-  if (valid) {
-    const int nh = s_cnt[0][lane];
-    float* sl = p.slope + (size_t)h * N;
-    for (int v = q; v + 1 < nh; v += kSeg) {
-      const int a = row[v], b = row[v + 1];
-      const double ya = (double)__ldg(y + (size_t)a * K), yb = (double)__ldg(y + (size_t)b * K);
-      sl[v] = (float)(__ddiv_rn(__dsub_rn(yb, ya), __dmul_rn((double)(b - a), p.delta)));
+  // 2. join the lanes' hulls pairwise: groups of 2, 4, ..., 32 lanes
+  for (int d = 1; d < 32; d <<= 1) {
+    if ((lane & (2 * d - 1)) == 0) {
+      const int gl = lane, gm = lane + d, ge = lane + 2 * d;
+      // right end of the left group, left end of the right group
+      int la = -1, ia = 0, lb = -1, ib = 0;
+      for (int q = gm - 1; q >= gl; --q)
+        if (v.hi[q] > v.lo[q]) {
+          la = q;
+          ia = v.hi[q] - 1;
+          break;
+        }
+      for (int q = gm; q < ge; ++q)
+        if (v.hi[q] > v.lo[q]) {
+          lb = q;
+          ib = v.lo[q];
+          break;
+        }
+      if (la >= 0 && lb >= 0) {
+        float xa = v.st[la * c + ia], ya = v.val(la * c + ia);
+        float xb = v.st[lb * c + ib], yb = v.val(lb * c + ib);
+        for (bool moved = true; moved;) {
+          moved = false;
+          for (;;) {  // left end point on or below the chord (its predecessor, right end)?
+            int lp = la, ip = ia;
+            v.prev(lp, ip, gl);
+            if (lp < 0) break;
+            const float xp = v.st[lp * c + ip], yp = v.val(lp * c + ip);
+            if (!below_chord(yp, ya, yb, xp, xa, xb)) break;
+            la = lp;
+            ia = ip;
+            xa = xp;
+            ya = yp;
+            moved = true;
+          }
+          for (;;) {  // right end point on or below the chord (left end, its successor)?
+            int ln = lb, in = ib;
+            v.next(ln, in, ge);
+            if (ln < 0) break;
+            const float xn = v.st[ln * c + in], yn = v.val(ln * c + in);
+            if (!below_chord(ya, yb, yn, xa, xb, xn)) break;
+            lb = ln;
+            ib = in;
+            xb = xn;
+            yb = yn;
+            moved = true;
+          }
+        }
+        v.hi[la] = ia + 1;
+        for (int q = la + 1; q < gm; ++q) v.hi[q] = v.lo[q];
+        for (int q = gm; q < lb; ++q) v.hi[q] = v.lo[q];
+        v.lo[lb] = ib;
+      }
+    }
+    __syncwarp();
+  }
+
+  // 3. read-out: vertex q of the envelope lies in the last lane whose
+  // exclusive prefix of kept counts is <= q (empty lanes share the prefix of
+  // the next non-empty one, so that lane is never empty)
+  const int kept = v.hi[lane] - v.lo[lane];
+  int pre = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, pre, o);
+    if (lane >= o) pre += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, pre, 31);
+  s_pre[w][lane] = pre - kept;
+  if (lane == 0) p.n_bp[h] = total;
+  __syncwarp();
+  auto position = [&](int q) {  // stack position of vertex q
+    int L = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (s_pre[w][L + step] <= q) L += step;
+    return L * c + v.lo[L] + q - s_pre[w][L];
+  };
+  if constexpr (kStaged) {
+    for (int q = lane; q < total; q += 32) {
+      const int pa = position(q);
+      const float xa = v.st[pa];
+      row[q] = (int)xa;
+      if (q + 1 < total) {
+        const int pb = position(q + 1);
+        sl[q] = hull_slope(xa, v.sv[pa], v.st[pb], v.sv[pb], p.delta);
+      }
+    }
+  } else {
+    for (int q = lane; q < total; q += 32) row[q] = (int)v.st[position(q)];
+    __syncwarp();  // the slope row held the stacks
+    for (int q = lane; q + 1 < total; q += 32) {
+      const int a = row[q], b = row[q + 1];
+      sl[q] = hull_slope((float)a, v.point(a), (float)b, v.point(b), p.delta);
     }
   }
 }
@@ -252,7 +414,18 @@ __global__ void ev_restore_kernel(float* ev, const double* evoff, int MN, int K)
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream) {
   const int n_h = p.n_t * p.M * p.K;
   if (n_h == 0) return cudaSuccess;
-  hull_kernel<<<(n_h + 31) / 32, 32 * kSeg, 0, stream>>>(p);
+  const size_t per_warp = (size_t)p.N * 8;  // staged values and local hulls
+  int lg = 3;
+  while (lg > 0 && (per_warp << lg) > (size_t)kHullSmemBudget) --lg;
+  if ((per_warp << lg) <= (size_t)kHullSmemBudget) {
+    const int nw = 1 << lg, smem = (int)(per_warp << lg);
+    cudaError_t e = cudaFuncSetAttribute(hull_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    hull_kernel<true><<<(n_h + nw - 1) / nw, 32 * nw, smem, stream>>>(p, lg);
+  } else {
+    hull_kernel<false><<<(n_h + kHullWarps - 1) / kHullWarps, 32 * kHullWarps, 0, stream>>>(p, 3);
+  }
   return cudaGetLastError();
 }
 

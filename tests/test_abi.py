@@ -63,6 +63,7 @@ def _create(lib, asset, flags=0):
     ("A", 7, "A must equal"), ("n_modes", 3, "n_modes"), ("eta_c", 1.5, "efficiencies"),
     ("eta_d", 0.0, "efficiencies"), ("policy_bytes", 3, "policy_bytes"), ("N", 1, "N >= 2"),
     ("s0", 10_000, "s0"), ("K", 200, "supported"), ("s_max", -1.0, "s_max"),
+    ("N", (1 << 24) + 1, "2^24"),
 ])
 def test_invalid_asset_rejected_on_host(lib, field, value, needle):
     a = E.asset_from_instance(I.random_instance(0, 3, 20, 4, 2, 3))

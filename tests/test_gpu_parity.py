@@ -468,6 +468,24 @@ def test_bid_curves_wide_dynamic_range():
     _hull_gpu_vs_oracle(inst)
 
 
+@pytest.mark.parametrize("N", [2, 5, 33, 97, 1025, 13001])
+@pytest.mark.parametrize("shape", ["concave", "convex", "wave"])
+def test_bid_curves_envelope_shapes(N, shape):
+    """Envelopes whose every point is a vertex (concave), with only the end
+    points as vertices (convex) or with alternating runs (wave), on grids
+    narrower than a warp and wider than 32 points per lane: the bridges
+    between partial hulls cross many empty and trimmed parts.  The longest
+    grid does not fit the staged kernel's shared memory and runs the in-place
+    variant."""
+    D = min(2, N - 1)
+    inst = I.random_instance(90 + N, 2, N, 3, D, D, 1, cost="zero", terminal="random")
+    x = np.linspace(-1.0, 1.0, N)
+    f = {"concave": -x * x, "convex": x * x, "wave": np.sin(7.0 * x) + 0.3 * x}[shape]
+    inst.terminal[:] = (100.0 * f).astype(np.float32)[None, :, None]
+    inst.price[:] = np.float32(0.0)
+    _hull_gpu_vs_oracle(inst)
+
+
 # ------------------------------------------------- torch.autograd.Function
 
 def test_autograd_objective_matches_oracle_adjoint():
