@@ -259,6 +259,17 @@ int esdp_solve_noalloc(const esdp_asset* asset, const float* price, const float*
                        const float* cost, const float* terminal, float* V1, void* policy,
                        void* stream, char* err, int32_t err_len);
 
+/* Issue-rate probe of the float32 instructions of the max-plus loop (a
+ * register-only kernel, one block of 1024 threads per SM of the current
+ * device, clock64-timed): kind 0 add.f32, 1 add.rn.f32x2, 2 max.f32,
+ * 3 three-input max.f32, 4 the loop's mix (two packed adds and two
+ * three-input maxima per four evaluations).  Writes the median over SMs of
+ * warp-lane instructions and of element operations (adds, maxima or
+ * evaluations) per SM clock.  Blocks until done.  Returns ESDP_EINVAL for a
+ * bad kind, iters < 1 or a NULL output, ESDP_ECUDA on a CUDA error. */
+int esdp_alu_probe(int32_t kind, int32_t iters, double* instr_per_clk, double* elem_per_clk,
+                   void* stream);
+
 void esdp_destroy(esdp_ctx* ctx);
 const char* esdp_last_error(const esdp_ctx* ctx);
 int esdp_version(void);

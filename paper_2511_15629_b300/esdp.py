@@ -36,7 +36,7 @@ ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
            "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_iid_bids",
-           "esdp_iid_clear", "esdp_autotune",
+           "esdp_iid_clear", "esdp_autotune", "esdp_alu_probe",
            "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
 
 
@@ -84,6 +84,8 @@ def load_library():
     lib.esdp_last_error.argtypes = [vp]
     lib.esdp_last_error.restype = ctypes.c_char_p
     lib.esdp_version.argtypes = []
+    lib.esdp_alu_probe.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS:
         if name not in ("esdp_destroy", "esdp_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -434,3 +436,17 @@ def solve_noalloc(inst, price, trans, cost, terminal, V1, policy=None, stream=No
             _dev_ptr(V1), _dev_ptr(policy), _stream(stream), err, len(err))
     if rc != ESDP_OK:
         raise EsdpError(rc, err.value.decode())
+
+
+ALU_PROBE_KINDS = ("add.f32", "add.rn.f32x2", "max.f32", "max.f32 (3 inputs)", "max-plus mix")
+
+
+def alu_probe(kind: int, iters: int = 4096, stream=None):
+    """(instructions, element operations) per SM clock of one probe kind
+    (`ALU_PROBE_KINDS`), measured by the library's register-only kernel."""
+    lib = load_library()
+    ins, elem = ctypes.c_double(), ctypes.c_double()
+    rc = lib.esdp_alu_probe(kind, iters, ctypes.byref(ins), ctypes.byref(elem), _stream(stream))
+    if rc != ESDP_OK:
+        raise EsdpError(rc, "alu probe")
+    return ins.value, elem.value
