@@ -8,6 +8,8 @@ Pieces:
   * ``solve``      -- ctypes wrapper of the C backward induction (eq. 4-6 with
                       a Markov price chain, Alg. 1 in plain loops);
   * ``hull``       -- monotone-chain upper envelope (eq. 10-11);
+  * ``markov_bids_at`` -- price-quantity bids at one SoC state from that
+                      envelope, re-convexified over grid power (eq. 8-11);
   * ``occupancy``  -- forward state-occupancy pass and the envelope-theorem
                       gradients of J;
   * ``paper_alg1`` -- Algorithm 1 taken literally with numpy: the eq. 13 action
@@ -279,6 +281,60 @@ def paper_alg1(s_max: float, delta: float, p_max: float, eta: float, lam_hat: np
     if keep_policy:
         return V, pol, gap
     return V
+
+
+# --------------------------------------------------------------------------
+# Price-quantity bids at a SoC state from the Markov SoC envelope (eq. 8-11)
+# --------------------------------------------------------------------------
+
+def envelope_at(y: np.ndarray, h: np.ndarray, x: int) -> float:
+    """Value of the upper concave envelope (vertices h of y) at grid point x:
+    y at a vertex, else the chord of the two vertices around x,
+    y_a + ((y_b - y_a) (x - a)) / (b - a)."""
+    j = int(np.searchsorted(h, x))
+    if j < len(h) and h[j] == x:
+        return float(y[x])
+    a, b = int(h[j - 1]), int(h[j])
+    ya, yb = float(y[a]), float(y[b])
+    return ya + ((yb - ya) * float(x - a)) / float(b - a)
+
+
+def markov_bids_at(inst, y: np.ndarray, s: int):
+    """Bid curve at SoC index s from EV_t[m][.][k] = y [N] (eq. 8-11 on the
+    SoC envelope).  Candidate SoC points: the action window's ends
+    lo = max(0, s - D_dis), hi = min(N - 1, s + D_chg), s itself and the
+    envelope vertices strictly inside the window; each is mapped to grid
+    power (discharge, x <= s: p = (((s - x) delta) eta_d) / tau; charge,
+    x > s: p = (((s - x) delta) / eta_c) / tau) with U = envelope value.
+    Over ascending p the upper concave envelope of (p, U) is taken by the
+    monotone chain (a middle point is dropped when
+    (U_j - U_i)(p_l - p_i) - (U_l - U_i)(p_j - p_i) <= 0), and segment q sells
+    at -(U_{q+1} - U_q) / ((p_{q+1} - p_q) tau).  Returns (SoC indices of the
+    vertices, their powers in MW, the segment prices)."""
+    y = np.asarray(y, dtype=np.float64)
+    N = len(y)
+    h = hull(y)
+    delta = inst.s_max / (N - 1)
+    lo, hi = max(0, s - inst.D_dis), min(N - 1, s + inst.D_chg)
+    xs = sorted({lo, hi, s} | {int(v) for v in h if lo < v < hi}, reverse=True)
+    pts = []
+    for x in xs:  # descending SoC = ascending power
+        if x <= s:
+            p = (((s - x) * delta) * inst.eta_d) / inst.tau
+        else:
+            p = (((s - x) * delta) / inst.eta_c) / inst.tau
+        pts.append((x, p, envelope_at(y, h, x)))
+    chain = []
+    for x, p, u in pts:
+        while len(chain) >= 2:
+            (_, pi, ui), (_, pj, uj) = chain[-2], chain[-1]
+            if (uj - ui) * (p - pi) - (u - ui) * (pj - pi) > 0.0:
+                break
+            chain.pop()
+        chain.append((x, p, u))
+    prices = [-(chain[q + 1][2] - chain[q][2]) / ((chain[q + 1][1] - chain[q][1]) * inst.tau)
+              for q in range(len(chain) - 1)]
+    return [c[0] for c in chain], [c[1] for c in chain], prices
 
 
 # --------------------------------------------------------------------------

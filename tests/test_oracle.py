@@ -662,3 +662,106 @@ def test_paper_clear_reproduces_dp_value_in_expectation():
     se = revs.std(ddof=1) / math.sqrt(n)
     target = V[0][int(round(s0 / prob.delta))]
     assert abs(revs.mean() - target) <= 3 * se + 1e-9, (revs.mean(), target, se)
+
+
+# ------------------------------------ Markov bids at a SoC state (eq. 8-11)
+
+def _bid_inst(N, D_dis, D_chg, eta_c, eta_d, s_max=4.0, tau=0.25):
+    inst = I.random_instance(0, 2, N, 2, D_dis, D_chg, 1)
+    inst.eta_c, inst.eta_d, inst.s_max, inst.tau = eta_c, eta_d, s_max, tau
+    return inst
+
+
+def test_markov_bids_linear_value_closed_form():
+    """EV linear in SoC with marginal value g per MWh of stored energy, s
+    inside the window: buying grid energy adds g eta_c per MWh, selling needs
+    g / eta_d per MWh.  For g > 0 the two sides are monotone (g eta_c <
+    g / eta_d) and s stays a vertex; for g < 0 they cross and the re-hull over
+    power merges them into one segment at the average
+    g (hi - lo) / ((s - lo) eta_d + (hi - s) / eta_c)."""
+    N, Dd, Dc, ec, ed = 61, 7, 11, 0.9, 0.8
+    inst = _bid_inst(N, Dd, Dc, ec, ed)
+    delta = inst.s_max / (N - 1)
+    s, lo, hi = 30, 30 - Dd, 30 + Dc
+    for g in (37.0, -12.0):
+        y = g * delta * np.arange(N)
+        xs, ps, prices = O.markov_bids_at(inst, y, s)
+        if g > 0:
+            assert xs == [hi, s, lo]
+            assert prices == pytest.approx([g * ec, g / ed], rel=1e-12)
+            assert ps == pytest.approx([-(hi - s) * delta / (ec * inst.tau), 0.0,
+                                        (s - lo) * delta * ed / inst.tau], rel=1e-12)
+        else:
+            assert xs == [hi, lo]
+            assert prices == pytest.approx([g * (hi - lo) / ((s - lo) * ed + (hi - s) / ec)],
+                                           rel=1e-12)
+
+
+def test_markov_bids_unit_efficiency_are_soc_slopes():
+    """eta_c = eta_d = 1: power is linear in SoC on both sides, so the bid
+    vertices are the window's ends and the SoC-envelope vertices inside it,
+    and every price is the envelope slope of its SoC segment."""
+    rng = np.random.default_rng(4)
+    N = 80
+    inst = _bid_inst(N, 12, 9, 1.0, 1.0)
+    delta = inst.s_max / (N - 1)
+    for trial in range(6):
+        y = np.cumsum(rng.normal(1.0, 4.0, size=N)).astype(np.float32).astype(np.float64)
+        s = int(rng.integers(0, N))
+        lo, hi = max(0, s - 12), min(N - 1, s + 9)
+        h = O.hull(y)
+        xs, _, prices = O.markov_bids_at(inst, y, s)
+        expect = sorted({lo, hi} | {int(v) for v in h if lo < v < hi}, reverse=True)
+        env = np.interp(np.arange(N), h, y[h])
+        want = [(env[a] - env[b]) / ((a - b) * delta) for a, b in zip(xs, xs[1:])]
+        assert prices == pytest.approx(want, rel=1e-9, abs=1e-9)
+        if xs != expect:
+            # s on an envelope segment is collinear in exact arithmetic; its
+            # interpolated value may round above the chord, which leaves it as
+            # a vertex between two equal prices
+            q = xs.index(s)
+            assert s not in expect and [x for x in xs if x != s] == expect
+            assert prices[q - 1] == pytest.approx(prices[q], rel=1e-9, abs=1e-9)
+
+
+def test_markov_bids_envelope_and_merit_order_by_brute_force():
+    """Vertices are exactly the candidate points above every chord (exact
+    rationals), prices never fall, and at any price lam the curve clears the
+    power that maximises lam p tau + E(s + shift(p)) over every grid point of
+    the window (E the SoC envelope, taken by linear interpolation of the
+    envelope vertices)."""
+    rng = np.random.default_rng(12)
+    N = 70
+    for trial in range(8):
+        Dd, Dc = int(rng.integers(0, 20)), int(rng.integers(0, 20))
+        ec, ed = float(rng.uniform(0.8, 1.0)), float(rng.uniform(0.8, 1.0))
+        inst = _bid_inst(N, Dd, Dc, ec, ed, tau=float(rng.choice([1.0, 0.25])))
+        delta = inst.s_max / (N - 1)
+        y = np.cumsum(rng.normal(0.5, 3.0, size=N)).astype(np.float32).astype(np.float64)
+        s = int(rng.integers(0, N))
+        lo, hi = max(0, s - Dd), min(N - 1, s + Dc)
+        xs, ps, prices = O.markov_bids_at(inst, y, s)
+        assert all(b >= a for a, b in zip(prices, prices[1:]))
+        h = O.hull(y)
+        env = np.interp(np.arange(N), h, y[h])
+
+        def power(x):
+            e = (s - x) * delta
+            return (e * ed if x <= s else e / ec) / inst.tau
+        # candidate points in ascending power, exact-rational envelope test
+        cand = sorted({lo, hi, s} | {int(v) for v in h if lo < v < hi}, reverse=True)
+        P = [Fraction(power(x)) for x in cand]
+        U = [Fraction(float(O.envelope_at(y, h, x))) for x in cand]
+        brute = [cand[0]] + [cand[i] for i in range(1, len(cand) - 1)
+                             if all(U[i] > U[j] + (U[l] - U[j]) * (P[i] - P[j]) / (P[l] - P[j])
+                                    for j in range(i) for l in range(i + 1, len(cand)))]
+        if len(cand) > 1:
+            brute.append(cand[-1])
+        assert xs == brute
+        # merit order
+        window = range(lo, hi + 1)
+        for lam in rng.uniform(-80.0, 80.0, size=25):
+            best = max(lam * power(x) * inst.tau + env[x] for x in window)
+            q = sum(1 for pr in prices if pr < lam)
+            got = lam * ps[q] * inst.tau + O.envelope_at(y, h, xs[q])
+            assert got == pytest.approx(best, rel=1e-10, abs=1e-9)
