@@ -569,6 +569,42 @@ def bench_bids_clearing(torch, E, I, stream, flush, args, n_sm, f_max):
             "mean_revenue_per_path": float(rev.mean()), "V0_at_s0": float(V0[1000])}
 
 
+def bench_bids_at(torch, E, I, stream, flush, args, n_sm, f_max):
+    """config2: price-quantity bids at the initial SoC for every (stage, mode,
+    price state) from the SoC envelopes (esdp_bids_at after the solve and
+    esdp_bid_curves), median of 10 launches, L2 flushed before each."""
+    inst = I.config2()
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    s = E.Solver([inst], device_ptrs=True, keep_ev=True)
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    sh = (inst.T, inst.n_modes, inst.K)
+    n_bp = torch.empty(sh, dtype=torch.int32, device="cuda")
+    idx = torch.empty(sh + (inst.N,), dtype=torch.int32, device="cuda")
+    slope = torch.empty(sh + (inst.N,), dtype=torch.float32, device="cuda")
+    n_pts = torch.empty(sh, dtype=torch.int32, device="cuda")
+    p_mw = torch.empty(sh + (inst.A,), dtype=torch.float64, device="cuda")
+    price = torch.empty(sh + (inst.A,), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+    s.bid_curves(0, 1, inst.T + 1, n_bp, idx, slope, stream=st)
+    ts = []
+    for i in range(13):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.bids_at(0, 1, inst.T + 1, inst.s0, n_bp, idx, n_pts, p_mw, price, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if i >= 3:
+            ts.append(e0.elapsed_time(e1))
+    s.close()
+    ts.sort()
+    return {"workload": "config2 bids at s0 for 288 x 2 x 20 (stage, mode, state)",
+            "bids_at_ms": ts[len(ts) // 2],
+            "mean_breakpoints": float(n_pts.float().mean().item())}
+
+
 def bench_alu_probe(torch, E, I, stream, flush, args, n_sm, f_max):
     """Issue rates of the float32 instructions the max-plus loop is made of
     (register-only kernel, clock64-timed, median over SMs), against the
@@ -584,7 +620,7 @@ def bench_alu_probe(torch, E, I, stream, flush, args, n_sm, f_max):
 
 EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
           "paper_table3": bench_table3, "paper_bids_clearing": bench_bids_clearing,
-          "alu_probe": bench_alu_probe}
+          "alu_probe": bench_alu_probe, "config2_bids_at": bench_bids_at}
 
 
 def run_profile_case(name):

@@ -117,6 +117,29 @@ int esdp_expected_value(esdp_ctx* ctx, int32_t asset, int32_t t, float* out, voi
 int esdp_bid_curves(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
                     int32_t* bp_idx, float* slope, void* stream);
 
+/* Price-quantity bids at SoC index s (0..N-1) for stages t0..t1-1 of an
+ * asset (eq. 8-11 on the SoC envelope): for every (stage, mode, price state)
+ * the envelope vertices that esdp_bid_curves returned for the same stages
+ * and lie inside the action window [s - D_dis, s + D_chg] (clipped to the
+ * grid), the window's two ends and s itself (values on the envelope, chords
+ * interpolated) are mapped to grid power -- selling, x <= s:
+ * p = (s - x) delta eta_d / tau; buying, x > s: p = (s - x) delta / (eta_c tau)
+ * -- and the upper concave envelope of U(p) = E_t(x(p)) is taken over power.
+ * Segment q, between breakpoints p_mw[q] < p_mw[q+1] (MW, ascending: buying
+ * first), sells at price[q] = -(U_{q+1} - U_q) / ((p_{q+1} - p_q) tau) $/MWh,
+ * non-decreasing in q; where the buying price g eta_c of a marginal value g
+ * would exceed its selling price g / eta_d (g < 0) the envelope merges the
+ * two sides.  Inputs n_bp [n][M][K], bp_idx [n][M][K][N] as esdp_bid_curves
+ * wrote them (n = t1 - t0); outputs n_pts [n][M][K] (breakpoint count,
+ * >= 1), p_mw [n][M][K][A] (double), price [n][M][K][A] (float, the first
+ * n_pts - 1 used).  Needs ESDP_KEEP_EV and a completed solve.  Device or
+ * host pointers as the context's flags say; host mode blocks.  Returns
+ * ESDP_EINVAL (NULL pointer, bad asset, stage range or s), ESDP_ESTATE,
+ * ESDP_ENOMEM or ESDP_ECUDA. */
+int esdp_bids_at(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1, int32_t s,
+                 const int32_t* n_bp, const int32_t* bp_idx, int32_t* n_pts, double* p_mw,
+                 float* price, void* stream);
+
 /* Objective J = sum_k mu0[k] V_1[0][s0][k] (mode 0, initial SoC index s0 of
  * the asset) from the V_1 of the last esdp_solve, summed in double on the
  * device.  mu0 [K] is the initial price-state distribution; J [1] (double).

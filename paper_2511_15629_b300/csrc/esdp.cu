@@ -852,6 +852,81 @@ int esdp_bid_curves(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t*
   return ESDP_OK;
 }
 
+int esdp_bids_at(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t s_idx,
+                 const int32_t* n_bp, const int32_t* bp_idx, int32_t* n_pts, double* p_mw,
+                 float* price, void* stream) {
+  if (!c || !n_bp || !bp_idx || !n_pts || !p_mw || !price) return ESDP_EINVAL;
+  if (asset < 0 || asset >= (int32_t)c->assets.size())
+    return fail(c, ESDP_EINVAL, "asset index %d out of range", asset);
+  const esdp_asset& a = c->assets[asset];
+  if (t0 < 1 || t1 > a.T + 1 || t1 <= t0) return fail(c, ESDP_EINVAL, "bad stage range");
+  if (s_idx < 0 || s_idx >= a.N) return fail(c, ESDP_EINVAL, "SoC index %d outside the grid", s_idx);
+  if (!c->solved) return fail(c, ESDP_ESTATE, "no solve has completed");
+  if (!(c->flags & ESDP_KEEP_EV)) return fail(c, ESDP_ESTATE, "context made without ESDP_KEEP_EV");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = (c->flags & ESDP_DEVICE_PTRS) != 0;
+  const int n_t = t1 - t0;
+  const size_t L = mnk_of(a);
+  const size_t nh = (size_t)n_t * a.n_modes * a.K;
+  const int* d_nbp = n_bp;
+  const int* d_idx = bp_idx;
+  int* d_np = n_pts;
+  double* d_p = p_mw;
+  float* d_pr = price;
+  std::vector<void*> tmp;
+  if (!dev) {
+    const size_t sizes[5] = {nh * 4, nh * a.N * 4, nh * 4, nh * a.A * 8, nh * a.A * 4};
+    void* q[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 5; ++i)
+      if (cudaMalloc(&q[i], sizes[i]) != cudaSuccess) {
+        for (void* x : q) cudaFree(x);
+        cudaGetLastError();
+        return fail(c, ESDP_ENOMEM, "bid allocation failed");
+      }
+    tmp.assign(q, q + 5);
+    d_nbp = (const int*)q[0];
+    d_idx = (const int*)q[1];
+    d_np = (int*)q[2];
+    d_p = (double*)q[3];
+    d_pr = (float*)q[4];
+    cudaError_t e = cudaMemcpyAsync(q[0], n_bp, sizes[0], cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q[1], bp_idx, sizes[1], cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      for (void* x : tmp) cudaFree(x);
+      return cuda_fail(c, e, "bid inputs");
+    }
+  }
+  BidsAtParams bp{};
+  bp.ev = c->d_ev[asset] + (size_t)(t0 - 1) * L;
+  bp.n_bp = d_nbp;
+  bp.idx = d_idx;
+  bp.n_t = n_t;
+  bp.M = a.n_modes;
+  bp.N = a.N;
+  bp.K = a.K;
+  bp.s = s_idx;
+  bp.D_dis = a.D_dis;
+  bp.D_chg = a.D_chg;
+  bp.A = a.A;
+  bp.delta = a.s_max / (double)(a.N - 1);
+  bp.eta_c = a.eta_c;
+  bp.eta_d = a.eta_d;
+  bp.tau = a.tau;
+  bp.n_pts = d_np;
+  bp.p_mw = d_p;
+  bp.price = d_pr;
+  cudaError_t e = launch_bids_at(bp, st);
+  if (e == cudaSuccess && !dev) {
+    e = cudaMemcpyAsync(n_pts, d_np, nh * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p_mw, d_p, nh * a.A * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(price, d_pr, nh * a.A * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  for (void* x : tmp) cudaFree(x);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bids at a SoC state");
+  return ESDP_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ adjoint

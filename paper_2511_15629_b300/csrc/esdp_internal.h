@@ -172,6 +172,19 @@ struct HullParams {
   float* slope;      // [n_t][M][K][N]
 };
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream);
+// Price-quantity bids at SoC index s from the envelopes of the bid-curve
+// kernel (one thread per (stage, mode, price state)).
+struct BidsAtParams {
+  const float* ev;      // reported EV_t of stage t0 at ev, stage stride MNK, layout [M][N][K]
+  const int* n_bp;      // [n_t][M][K] envelope vertex counts
+  const int* idx;       // [n_t][M][K][N] envelope vertex indices
+  int n_t, M, N, K, s, D_dis, D_chg, A;
+  double delta, eta_c, eta_d, tau;
+  int* n_pts;           // [n_t][M][K] out
+  double* p_mw;         // [n_t][M][K][A] out
+  float* price;         // [n_t][M][K][A] out (first n_pts - 1 used)
+};
+cudaError_t launch_bids_at(const BidsAtParams& p, cudaStream_t stream);
 // Kept EV'_t of n_t stages -> reported EV_t = float(EV'_t + evoff_t[k]), in place.
 cudaError_t launch_ev_restore(float* ev, const double* evoff, int n_t, int MN, int K,
                               cudaStream_t stream);

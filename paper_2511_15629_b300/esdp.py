@@ -35,6 +35,7 @@ ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
+           "esdp_bids_at",
            "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_iid_bids",
            "esdp_iid_clear", "esdp_autotune", "esdp_alu_probe",
            "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
@@ -74,6 +75,7 @@ def load_library():
     lib.esdp_policy.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_expected_value.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_bid_curves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.esdp_bids_at.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.esdp_objective.argtypes = [vp, i32, vp, vp, vp]
     lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
@@ -242,6 +244,30 @@ class Solver:
                                               p(idx, np.int32), p(slope, np.float32),
                                               _stream(stream)))
         return n_bp, idx, slope
+
+    def bids_at(self, asset: int, t0: int, t1: int, s: int, n_bp, idx, n_pts=None, p_mw=None,
+                price=None, stream=None):
+        """Price-quantity bids at SoC index s (esdp_bids_at) from the envelopes
+        `n_bp`, `idx` of bid_curves over the same stages: (n_pts [n,M,K],
+        p_mw [n,M,K,A] MW ascending, price [n,M,K,A] $/MWh of each segment)."""
+        inst = self.instances[asset]
+        n = t1 - t0
+        if n_pts is None:
+            assert not self.device
+            n_pts = np.empty((n, inst.n_modes, inst.K), np.int32)
+            p_mw = np.empty((n, inst.n_modes, inst.K, inst.A), np.float64)
+            price = np.empty((n, inst.n_modes, inst.K, inst.A), np.float32)
+        if self.device:
+            p = lambda a, d: _dev_ptr(a)
+        else:
+            n_bp = np.ascontiguousarray(n_bp, dtype=np.int32)
+            idx = np.ascontiguousarray(idx, dtype=np.int32)
+            p = _host_ptr
+        self._check(self._lib.esdp_bids_at(self._ctx, asset, t0, t1, s, p(n_bp, np.int32),
+                                           p(idx, np.int32), p(n_pts, np.int32),
+                                           p(p_mw, np.float64), p(price, np.float32),
+                                           _stream(stream)))
+        return n_pts, p_mw, price
 
     def objective(self, asset: int, mu0, J=None, stream=None):
         """J = sum_k mu0[k] V_1[0][s0][k] of the last solve (double)."""

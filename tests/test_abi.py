@@ -79,6 +79,7 @@ def test_null_arguments(lib):
     assert lib.esdp_grad(None, 0, None, None, None, None, None, None, None, None, None,
                          None) == E.ESDP_EINVAL
     assert lib.esdp_objective(None, 0, None, None, None) == E.ESDP_EINVAL
+    assert lib.esdp_bids_at(None, 0, 1, 2, 0, None, None, None, None, None, None) == E.ESDP_EINVAL
     lib.esdp_destroy(None)
 
 

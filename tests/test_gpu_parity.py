@@ -486,6 +486,73 @@ def test_bid_curves_envelope_shapes(N, shape):
     _hull_gpu_vs_oracle(inst)
 
 
+# ------------------------------------------------- bids at a SoC state
+
+@pytest.mark.parametrize("which", ["config2", "random"])
+def test_bids_at_match_oracle(which):
+    """esdp_bids_at against the oracle's markov_bids_at on the GPU's own EV:
+    breakpoint counts and powers identical (the same double operations),
+    prices identical after rounding to float32, prices non-decreasing."""
+    if which == "config2":
+        inst, T = I.config2(), 24            # the first day of 5-minute stages
+    else:
+        inst = I.random_instance(22, 6, 300, 5, 20, 35, 1, neg_prob=0.4, cost="nonconvex",
+                                 eta=(0.85, 0.9))
+        # stored energy left at the end costs $30/MWh: negative marginal values
+        # in the last stages, where buying would pay more than selling
+        x = np.arange(inst.N) * (inst.s_max / (inst.N - 1))
+        inst.terminal[:] = (-30.0 * x).astype(np.float32)[None, :, None]
+        T = inst.T
+    s, V1 = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, _ = s.bid_curves(0, 1, T + 1)
+    ev = np.stack([s.expected_value(0, t) for t in range(1, T + 1)])
+    merged = 0
+    for s_idx in (0, inst.N // 3, inst.N - 1):
+        n_pts, p_mw, price = s.bids_at(0, 1, T + 1, s_idx, n_bp, idx)
+        for t in range(T):
+            for m in range(inst.n_modes):
+                for k in range(inst.K):
+                    xs, ps, prs = O.markov_bids_at(inst, ev[t, m, :, k], s_idx)
+                    n = n_pts[t, m, k]
+                    assert n == len(xs)
+                    np.testing.assert_array_equal(p_mw[t, m, k, :n], ps)
+                    np.testing.assert_array_equal(price[t, m, k, :n - 1],
+                                                  np.asarray(prs, np.float64).astype(np.float32))
+                    assert np.all(np.diff(price[t, m, k, :n - 1]) >= 0)
+                    merged += 0.0 not in ps
+    if which == "random":
+        assert merged > 0   # negative marginal values: some curves merge the two sides
+
+
+def test_bids_at_device_pointers_equal_host():
+    import torch
+    inst = I.random_instance(23, 5, 200, 4, 15, 15, 2, neg_prob=0.3)
+    hs, _ = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, _ = hs.bid_curves(0, 1, inst.T + 1)
+    ref = hs.bids_at(0, 1, inst.T + 1, 77, n_bp, idx)
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).cuda() for k, v in cat.items()}
+    ds = E.Solver([inst], device_ptrs=True, keep_ev=True)
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    ds.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    sh = (inst.T, inst.n_modes, inst.K)
+    dn = torch.empty(sh, dtype=torch.int32, device="cuda")
+    di = torch.empty(sh + (inst.N,), dtype=torch.int32, device="cuda")
+    dsl = torch.empty(sh + (inst.N,), dtype=torch.float32, device="cuda")
+    ds.bid_curves(0, 1, inst.T + 1, dn, di, dsl)
+    n_pts = torch.empty(sh, dtype=torch.int32, device="cuda")
+    p_mw = torch.empty(sh + (inst.A,), dtype=torch.float64, device="cuda")
+    price = torch.empty(sh + (inst.A,), dtype=torch.float32, device="cuda")
+    ds.bids_at(0, 1, inst.T + 1, 77, dn, di, n_pts, p_mw, price)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(n_pts.cpu().numpy(), ref[0])
+    n = ref[0]
+    for i in np.ndindex(*sh):
+        np.testing.assert_array_equal(p_mw.cpu().numpy()[i][:n[i]], ref[1][i][:n[i]])
+        np.testing.assert_array_equal(price.cpu().numpy()[i][:n[i] - 1], ref[2][i][:n[i] - 1])
+    ds.close()
+
+
 # ------------------------------------------------- torch.autograd.Function
 
 def test_autograd_objective_matches_oracle_adjoint():
