@@ -373,6 +373,36 @@ def run_esdp(args, rank, world):
 
 # ---------------------------------------------------------- sub-benchmarks
 
+def bench_config1(torch, E, I, stream, flush, args, n_sm, f_max):
+    """The small day-ahead case (T=24, N=101, K=5, A=51): ~26k evaluations
+    per stage, so the solve is bound by launch and per-stage synchronisation
+    latency; reported as microseconds per solve and per stage, no roofline
+    fraction.  Median of 20 solves (L2 flushed before each)."""
+    inst = I.config1()
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    s.autotune(stream=stream)
+    st = torch.cuda.current_stream()
+    ts = []
+    for i in range(25):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if i >= 5:
+            ts.append(e0.elapsed_time(e1) * 1e3)
+    info = s.launch_info()
+    s.close()
+    ts.sort()
+    us = ts[len(ts) // 2]
+    return {"us_per_solve": us, "us_per_stage": us / inst.T, "evals_per_s": inst.evals / us * 1e6,
+            "launch": info}
+
+
 def bench_config3(torch, E, I, stream, flush, args, n_sm, f_max):
     """Large single asset: the persistent sweep alone (policy kept)."""
     inst = I.config3()
@@ -618,7 +648,7 @@ def bench_alu_probe(torch, E, I, stream, flush, args, n_sm, f_max):
     return out
 
 
-EXTRAS = {"config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
+EXTRAS = {"config1": bench_config1, "config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
           "paper_table3": bench_table3, "paper_bids_clearing": bench_bids_clearing,
           "alu_probe": bench_alu_probe, "config2_bids_at": bench_bids_at}
 
