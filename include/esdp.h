@@ -117,6 +117,21 @@ int esdp_expected_value(esdp_ctx* ctx, int32_t asset, int32_t t, float* out, voi
 int esdp_bid_curves(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
                     int32_t* bp_idx, float* slope, void* stream);
 
+/* The same bid curves in packed form, without the padding of the per-
+ * envelope rows: envelope h = ((t - t0) M + m) K + k owns entries
+ * [offsets[h], offsets[h+1]) of bp_idx (its vertex SoC indices, ascending)
+ * and of slope (the slope from each vertex to the next, $ per MWh of stored
+ * energy; the envelope's last entry is 0).  offsets [n_h + 1] (int64,
+ * offsets[0] = 0, offsets[n_h] = total vertices), bp_idx / slope [cap].
+ * Host mode: copies back the offsets and exactly `total` entries, and
+ * returns ESDP_EINVAL (offsets written, nothing else) when total > cap.
+ * Device mode: stream-ordered, entries at or beyond cap are not written
+ * (read offsets[n_h] to size the arrays; cap = n_h * N always suffices).
+ * Needs ESDP_KEEP_EV and a completed solve.  Errors as esdp_bid_curves. */
+int esdp_bid_curves_packed(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1,
+                           int64_t* offsets, int32_t* bp_idx, float* slope, int64_t cap,
+                           void* stream);
+
 /* Price-quantity bids at SoC index s (0..N-1) for stages t0..t1-1 of an
  * asset (eq. 8-11 on the SoC envelope): for every (stage, mode, price state)
  * the envelope vertices that esdp_bid_curves returned for the same stages

@@ -88,6 +88,8 @@ struct esdp_ctx {
   float* d_obj_mu = nullptr;      // host-mode esdp_objective staging: mu0 (max K floats)
   double* d_obj_J = nullptr;      // ... and J
   int* d_status = nullptr;
+  void* bid_scr = nullptr;        // bid-curve scratch (host-mode outputs, packed form), grown on demand
+  size_t bid_scr_bytes = 0;
   // inputs of the last solve (device pointers)
   const float* last_price = nullptr;
   const float* last_trans = nullptr;
@@ -675,6 +677,7 @@ void esdp_destroy(esdp_ctx* c) {
   free_plan(&c->main);
   for (Plan& p : c->solo) free_plan(&p);
   for (void* p : c->allocs) cudaFree(p);
+  cudaFree(c->bid_scr);
   delete c;
 }
 
@@ -795,44 +798,41 @@ int esdp_expected_value(esdp_ctx* c, int32_t asset, int32_t t, float* out, void*
   return ESDP_OK;
 }
 
-int esdp_bid_curves(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
-                    int32_t* bp_idx, float* slope, void* stream) {
-  if (!c || !n_bp || !bp_idx || !slope) return ESDP_EINVAL;
+namespace {
+
+// Device scratch of the bid-curve entry points: grown on demand (the free of
+// a smaller one synchronises the device), kept until esdp_destroy.
+void* bid_scratch(esdp_ctx* c, size_t bytes) {
+  if (bytes <= c->bid_scr_bytes) return c->bid_scr;
+  cudaFree(c->bid_scr);
+  c->bid_scr = nullptr;
+  c->bid_scr_bytes = 0;
+  void* p = nullptr;
+  if (getenv("ESDP_FAIL_ALLOC") || cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->bid_scr = p;
+  c->bid_scr_bytes = bytes;
+  return p;
+}
+
+int check_bid_call(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1) {
   if (asset < 0 || asset >= (int32_t)c->assets.size())
     return fail(c, ESDP_EINVAL, "asset index %d out of range", asset);
   const esdp_asset& a = c->assets[asset];
   if (t0 < 1 || t1 > a.T + 1 || t1 <= t0) return fail(c, ESDP_EINVAL, "bad stage range");
   if (!c->solved) return fail(c, ESDP_ESTATE, "no solve has completed");
   if (!(c->flags & ESDP_KEEP_EV)) return fail(c, ESDP_ESTATE, "context made without ESDP_KEEP_EV");
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool dev = (c->flags & ESDP_DEVICE_PTRS) != 0;
-  const int n_t = t1 - t0;
-  const size_t L = mnk_of(a);
-  const size_t nh = (size_t)n_t * a.n_modes * a.K;
-  int* d_n = n_bp;
-  int* d_idx = bp_idx;
-  float* d_sl = slope;
-  std::vector<void*> tmp;
-  if (!dev) {
-    void* p1 = nullptr;
-    void* p2 = nullptr;
-    void* p3 = nullptr;
-    if (cudaMalloc(&p1, nh * 4) != cudaSuccess || cudaMalloc(&p2, nh * a.N * 4) != cudaSuccess ||
-        cudaMalloc(&p3, nh * a.N * 4) != cudaSuccess) {
-      cudaFree(p1);
-      cudaFree(p2);
-      cudaFree(p3);
-      cudaGetLastError();
-      return fail(c, ESDP_ENOMEM, "bid-curve output allocation failed");
-    }
-    d_n = (int*)p1;
-    d_idx = (int*)p2;
-    d_sl = (float*)p3;
-    tmp = {p1, p2, p3};
-  }
+  return ESDP_OK;
+}
+
+cudaError_t run_hull(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int* d_n, int* d_idx,
+                     float* d_sl, cudaStream_t st) {
+  const esdp_asset& a = c->assets[asset];
   HullParams hp{};
-  hp.ev = c->d_ev[asset] + (size_t)(t0 - 1) * L;
-  hp.n_t = n_t;
+  hp.ev = c->d_ev[asset] + (size_t)(t0 - 1) * mnk_of(a);
+  hp.n_t = t1 - t0;
   hp.M = a.n_modes;
   hp.N = a.N;
   hp.K = a.K;
@@ -840,15 +840,88 @@ int esdp_bid_curves(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t*
   hp.n_bp = d_n;
   hp.idx = d_idx;
   hp.slope = d_sl;
-  cudaError_t e = launch_hull(hp, st);
+  return launch_hull(hp, st);
+}
+
+}  // namespace
+
+int esdp_bid_curves(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int32_t* n_bp,
+                    int32_t* bp_idx, float* slope, void* stream) {
+  if (!c || !n_bp || !bp_idx || !slope) return ESDP_EINVAL;
+  int rc = check_bid_call(c, asset, t0, t1);
+  if (rc) return rc;
+  const esdp_asset& a = c->assets[asset];
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = (c->flags & ESDP_DEVICE_PTRS) != 0;
+  const size_t nh = (size_t)(t1 - t0) * a.n_modes * a.K;
+  int* d_n = n_bp;
+  int* d_idx = bp_idx;
+  float* d_sl = slope;
+  if (!dev) {
+    char* scr = (char*)bid_scratch(c, nh * 4 * (1 + 2 * (size_t)a.N));
+    if (!scr) return fail(c, ESDP_ENOMEM, "bid-curve scratch allocation failed");
+    d_n = (int*)scr;
+    d_idx = d_n + nh;
+    d_sl = (float*)(d_idx + nh * a.N);
+  }
+  cudaError_t e = run_hull(c, asset, t0, t1, d_n, d_idx, d_sl, st);
   if (e == cudaSuccess && !dev) {
     e = cudaMemcpyAsync(n_bp, d_n, nh * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bp_idx, d_idx, nh * a.N * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(slope, d_sl, nh * a.N * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
-  for (void* p : tmp) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(c, e, "bid curves");
+  return ESDP_OK;
+}
+
+int esdp_bid_curves_packed(esdp_ctx* c, int32_t asset, int32_t t0, int32_t t1, int64_t* offsets,
+                           int32_t* bp_idx, float* slope, int64_t cap, void* stream) {
+  if (!c || !offsets || !bp_idx || !slope || cap < 0) return ESDP_EINVAL;
+  int rc = check_bid_call(c, asset, t0, t1);
+  if (rc) return rc;
+  const esdp_asset& a = c->assets[asset];
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = (c->flags & ESDP_DEVICE_PTRS) != 0;
+  const size_t nh = (size_t)(t1 - t0) * a.n_modes * a.K;
+  const size_t rows = nh * (size_t)a.N;
+  // scratch: padded rows (counts, indices, slopes), then in host mode the
+  // offsets and the packed arrays (worst case: every point a vertex)
+  const size_t pad_bytes = (nh + 2 * rows) * 4;
+  const size_t off_at = (pad_bytes + 15) / 16 * 16;
+  const size_t bytes = dev ? pad_bytes : off_at + (nh + 1) * 8 + 2 * rows * 4;
+  char* scr = (char*)bid_scratch(c, bytes);
+  if (!scr) return fail(c, ESDP_ENOMEM, "bid-curve scratch allocation failed");
+  int* d_n = (int*)scr;
+  int* d_idx = d_n + nh;
+  float* d_sl = (float*)(d_idx + rows);
+  long long* d_off = (long long*)offsets;
+  int* d_pi = bp_idx;
+  float* d_ps = slope;
+  long long d_cap = cap;
+  if (!dev) {
+    d_off = (long long*)(scr + off_at);
+    d_pi = (int*)(d_off + nh + 1);
+    d_ps = (float*)(d_pi + rows);
+    d_cap = (long long)rows;
+  }
+  cudaError_t e = run_hull(c, asset, t0, t1, d_n, d_idx, d_sl, st);
+  if (e == cudaSuccess)
+    e = launch_pack_bids(d_n, d_idx, d_sl, a.N, (int)nh, d_off, d_cap, d_pi, d_ps, st);
+  if (e == cudaSuccess && !dev) {
+    e = cudaMemcpyAsync(offsets, d_off, (nh + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      const long long total = (long long)offsets[nh];
+      if (total > cap)
+        return fail(c, ESDP_EINVAL, "cap %lld is below the %lld vertices", (long long)cap, total);
+      e = cudaMemcpyAsync(bp_idx, d_pi, (size_t)total * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(slope, d_ps, (size_t)total * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "packed bid curves");
   return ESDP_OK;
 }
 

@@ -172,6 +172,12 @@ struct HullParams {
   float* slope;      // [n_t][M][K][N]
 };
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream);
+// Packed form of the bid curves: offsets[n_h + 1] (exclusive prefix of n_bp),
+// then each envelope's vertices and slopes copied to [offsets[h], offsets[h+1])
+// of idx_out / slope_out (entries at or beyond cap are not written).
+cudaError_t launch_pack_bids(const int* n_bp, const int* idx, const float* slope, int N, int n_h,
+                             long long* offsets, long long cap, int* idx_out, float* slope_out,
+                             cudaStream_t stream);
 // Price-quantity bids at SoC index s from the envelopes of the bid-curve
 // kernel (one thread per (stage, mode, price state)).
 struct BidsAtParams {

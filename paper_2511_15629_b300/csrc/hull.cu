@@ -409,6 +409,68 @@ __global__ void ev_restore_kernel(float* ev, const double* evoff, int MN, int K)
   }
 }
 
+// offsets[h] = sum of n_bp[0 .. h), offsets[n_h] = total: one block of 1024
+// threads walks the counts in chunks, each chunk scanned by warp shuffles
+// and a scan of the 32 warp sums, plus the running carry.
+__global__ void __launch_bounds__(1024) offsets_kernel(const int* n_bp, int n_h,
+                                                       long long* offsets) {
+  __shared__ long long s_warp[32];
+  __shared__ long long s_carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n_h; base += 1024) {
+    const int i = base + threadIdx.x;
+    const long long v = i < n_h ? n_bp[i] : 0;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      long long z = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      s_warp[lane] = z;  // inclusive scan of the warp sums
+    }
+    __syncthreads();
+    const long long carry = s_carry;
+    const long long excl = carry + (w ? s_warp[w - 1] : 0) + x - v;
+    if (i < n_h) offsets[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[n_h] = s_carry;
+}
+
+// one warp per envelope: its vertices and slopes from the padded rows to
+// [offsets[h], offsets[h+1]) of the packed arrays (the envelope's last slot
+// of `slope` is 0); nothing at or beyond cap is written
+__global__ void pack_kernel(const int* n_bp, const int* idx, const float* slope, int N, int n_h,
+                            const long long* offsets, long long cap, int* idx_out,
+                            float* slope_out) {
+  const int h = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (h >= n_h) return;
+  const int n = n_bp[h];
+  const long long o = offsets[h];
+  const int* row = idx + (size_t)h * N;
+  const float* sl = slope + (size_t)h * N;
+  for (int j = lane; j < n; j += 32) {
+    const long long d = o + j;
+    if (d >= cap) break;
+    idx_out[d] = row[j];
+    slope_out[d] = j + 1 < n ? sl[j] : 0.f;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream) {
@@ -440,4 +502,17 @@ cudaError_t launch_ev_restore(float* ev, const double* evoff, int n_t, int MN, i
   return cudaGetLastError();
 }
 
+cudaError_t launch_pack_bids(const int* n_bp, const int* idx, const float* slope, int N, int n_h,
+                             long long* offsets, long long cap, int* idx_out, float* slope_out,
+                             cudaStream_t stream) {
+  offsets_kernel<<<1, 1024, 0, stream>>>(n_bp, n_h, offsets);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_h == 0) return e;
+  const int warps_per_block = 8;
+  pack_kernel<<<(n_h + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, stream>>>(
+      n_bp, idx, slope, N, n_h, offsets, cap, idx_out, slope_out);
+  return cudaGetLastError();
+}
+
 }  // namespace esdp
+

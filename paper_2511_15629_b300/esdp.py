@@ -35,7 +35,7 @@ ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
-           "esdp_bids_at",
+           "esdp_bids_at", "esdp_bid_curves_packed",
            "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_iid_bids",
            "esdp_iid_clear", "esdp_autotune", "esdp_alu_probe",
            "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
@@ -76,6 +76,7 @@ def load_library():
     lib.esdp_expected_value.argtypes = [vp, i32, i32, vp, vp]
     lib.esdp_bid_curves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
     lib.esdp_bids_at.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.esdp_bid_curves_packed.argtypes = [vp, i32, i32, i32, vp, vp, vp, ctypes.c_int64, vp]
     lib.esdp_objective.argtypes = [vp, i32, vp, vp, vp]
     lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
@@ -244,6 +245,33 @@ class Solver:
                                               p(idx, np.int32), p(slope, np.float32),
                                               _stream(stream)))
         return n_bp, idx, slope
+
+    def bid_curves_packed(self, asset: int, t0: int, t1: int, offsets=None, idx=None, slope=None,
+                          stream=None):
+        """Bid curves without row padding (esdp_bid_curves_packed): envelope h
+        owns [offsets[h], offsets[h+1]) of idx and slope.  Host mode allocates
+        worst-case arrays when not given and returns views of `total`
+        entries; device mode writes the given tensors (cap = their length)."""
+        inst = self.instances[asset]
+        nh = (t1 - t0) * inst.n_modes * inst.K
+        if offsets is None:
+            assert not self.device
+            offsets = np.empty(nh + 1, np.int64)
+            idx = np.empty(nh * inst.N, np.int32)
+            slope = np.empty(nh * inst.N, np.float32)
+        if self.device:
+            cap = min(idx.numel(), slope.numel())
+            p = lambda a, d: _dev_ptr(a)
+        else:
+            cap = min(idx.size, slope.size)
+            p = _host_ptr
+        self._check(self._lib.esdp_bid_curves_packed(self._ctx, asset, t0, t1,
+                                                     p(offsets, np.int64), p(idx, np.int32),
+                                                     p(slope, np.float32), cap, _stream(stream)))
+        if not self.device:
+            total = int(offsets[-1])
+            return offsets, idx[:total], slope[:total]
+        return offsets, idx, slope
 
     def bids_at(self, asset: int, t0: int, t1: int, s: int, n_bp, idx, n_pts=None, p_mw=None,
                 price=None, stream=None):

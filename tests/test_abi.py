@@ -80,6 +80,7 @@ def test_null_arguments(lib):
                          None) == E.ESDP_EINVAL
     assert lib.esdp_objective(None, 0, None, None, None) == E.ESDP_EINVAL
     assert lib.esdp_bids_at(None, 0, 1, 2, 0, None, None, None, None, None, None) == E.ESDP_EINVAL
+    assert lib.esdp_bid_curves_packed(None, 0, 1, 2, None, None, None, 0, None) == E.ESDP_EINVAL
     lib.esdp_destroy(None)
 
 

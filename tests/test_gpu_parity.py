@@ -486,6 +486,52 @@ def test_bid_curves_envelope_shapes(N, shape):
     _hull_gpu_vs_oracle(inst)
 
 
+# ------------------------------------------------- packed bid curves
+
+def test_bid_curves_packed_equal_padded():
+    """Host and device packed forms hold exactly the padded rows' vertices and
+    slopes (the envelope's last slope slot 0); a cap below the vertex total is
+    rejected in host mode and truncates in device mode."""
+    import torch
+    inst = I.random_instance(24, 7, 333, 6, 25, 30, 2, neg_prob=0.3, cost="nonconvex")
+    s, _ = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, slope = s.bid_curves(0, 2, inst.T + 1)
+    off, pidx, psl = s.bid_curves_packed(0, 2, inst.T + 1)
+    n = n_bp.reshape(-1)
+    assert off[0] == 0 and np.array_equal(np.diff(off), n)
+    rows_i, rows_s = idx.reshape(len(n), -1), slope.reshape(len(n), -1)
+    for h in range(len(n)):
+        a, b = off[h], off[h + 1]
+        np.testing.assert_array_equal(pidx[a:b], rows_i[h, :n[h]])
+        np.testing.assert_array_equal(psl[a:b - 1], rows_s[h, :n[h] - 1])
+        assert psl[b - 1] == 0.0
+    with pytest.raises(E.EsdpError) as ei:
+        s.bid_curves_packed(0, 2, inst.T + 1, np.empty(len(n) + 1, np.int64),
+                            np.empty(int(off[-1]) - 1, np.int32), np.empty(int(off[-1]) - 1, np.float32))
+    assert ei.value.code == E.ESDP_EINVAL
+    # device pointers
+    cat = E.concat_inputs([inst])
+    d = {k: torch.from_numpy(v).cuda() for k, v in cat.items()}
+    ds = E.Solver([inst], device_ptrs=True, keep_ev=True)
+    V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+    ds.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    doff = torch.empty(len(n) + 1, dtype=torch.int64, device="cuda")
+    total = int(off[-1])
+    di = torch.full((total,), -7, dtype=torch.int32, device="cuda")
+    dsl = torch.empty(total, dtype=torch.float32, device="cuda")
+    ds.bid_curves_packed(0, 2, inst.T + 1, doff, di, dsl)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(doff.cpu().numpy(), off)
+    np.testing.assert_array_equal(di.cpu().numpy(), pidx)
+    np.testing.assert_array_equal(dsl.cpu().numpy(), psl)
+    short = torch.full((total - 5,), -7, dtype=torch.int32, device="cuda")
+    shs = torch.empty(total - 5, dtype=torch.float32, device="cuda")
+    ds.bid_curves_packed(0, 2, inst.T + 1, doff, short, shs)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(short.cpu().numpy(), pidx[:total - 5])
+    ds.close()
+
+
 # ------------------------------------------------- bids at a SoC state
 
 @pytest.mark.parametrize("which", ["config2", "random"])
