@@ -80,6 +80,22 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+// a * b + c per lane of a float pair (two round-to-nearest FMAs)
+__device__ __forceinline__ float2 fma2u(unsigned long long a, unsigned long long b,
+                                        unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+  return f;
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float r;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -210,15 +226,28 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
         }
         const float2* Br = BP + rr * Pp;
         if constexpr (!kPol) {
-          // four actions per step: two 16-byte reads of (next value, payoff)
+          // four actions per step: two 16-byte reads of (next value, payoff);
+          // each packed FMA forms two samples' candidates of one action (two
+          // round-to-nearest FMAs, the same values as scalar fmaf)
           const float4* B4 = reinterpret_cast<const float4*>(Br);
+          unsigned long long lam2[kIidKG / 2];
+#pragma unroll
+          for (int j = 0; j < kIidKG / 2; ++j) lam2[j] = pack2(lam[2 * j], lam[2 * j + 1]);
 #pragma unroll 2
           for (int q = 0; q < (Pp >> 1); q += 2) {
             const float4 x = B4[q], y = B4[q + 1];
+            const unsigned long long b0 = pack2(x.x, x.x), p0 = pack2(x.y, x.y);
+            const unsigned long long b1 = pack2(x.z, x.z), p1 = pack2(x.w, x.w);
+            const unsigned long long b2 = pack2(y.x, y.x), p2 = pack2(y.y, y.y);
+            const unsigned long long b3 = pack2(y.z, y.z), p3 = pack2(y.w, y.w);
 #pragma unroll
-            for (int j = 0; j < kIidKG; ++j) {
-              best[j] = max3f(best[j], fmaf(lam[j], x.y, x.x), fmaf(lam[j], x.w, x.z));
-              best[j] = max3f(best[j], fmaf(lam[j], y.y, y.x), fmaf(lam[j], y.w, y.z));
+            for (int j = 0; j < kIidKG / 2; ++j) {
+              const float2 c0 = fma2u(lam2[j], p0, b0), c1 = fma2u(lam2[j], p1, b1);
+              const float2 c2 = fma2u(lam2[j], p2, b2), c3 = fma2u(lam2[j], p3, b3);
+              best[2 * j] = max3f(best[2 * j], c0.x, c1.x);
+              best[2 * j + 1] = max3f(best[2 * j + 1], c0.y, c1.y);
+              best[2 * j] = max3f(best[2 * j], c2.x, c3.x);
+              best[2 * j + 1] = max3f(best[2 * j + 1], c2.y, c3.y);
             }
           }
         } else {
