@@ -219,9 +219,19 @@ def cpu_baseline_c2():
     r = O.solve(inst, keep_EV=True, nthreads=cores)
     O.bid_curves(inst, r["EV"])
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on the first 48 stages (a bounded sample)
+    import copy
+    part = copy.copy(inst)
+    part.T = 48
+    part.price, part.trans = inst.price[:48].copy(), inst.trans[:48].copy()
+    t1 = time.perf_counter()
+    O.solve(part, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": inst.evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "one full config2 step (FP64 solve with policy + 11520 envelopes), "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "single_thread": {"value": part.evals / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"config2 stages 1-48, FP64 solve with policy, {dt1:.1f} s"}}
 
 
 def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
