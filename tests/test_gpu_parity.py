@@ -570,6 +570,36 @@ def test_bids_at_match_oracle(which):
         assert merged > 0   # negative marginal values: some curves merge the two sides
 
 
+@pytest.mark.parametrize("N,Dd,Dc,modes", [
+    (2, 1, 1, 1),        # two SoC points
+    (40, 0, 6, 1),       # charge only: the window ends at s
+    (40, 6, 0, 2),       # discharge only
+    (33, 32, 32, 1),     # window wider than the grid on both sides
+    (129, 3, 40, 2),     # asymmetric band
+])
+def test_bids_at_edge_windows(N, Dd, Dc, modes):
+    inst = I.random_instance(40 + N, 4, N, 3, Dd, Dc, modes, neg_prob=0.3, cost="nonconvex",
+                             eta=(0.88, 0.93))
+    s, _ = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, _ = s.bid_curves(0, 1, inst.T + 1)
+    ev = np.stack([s.expected_value(0, t) for t in range(1, inst.T + 1)])
+    for s_idx in sorted({0, N // 2, N - 1}):
+        n_pts, p_mw, price = s.bids_at(0, 1, inst.T + 1, s_idx, n_bp, idx)
+        for t in range(inst.T):
+            for m in range(inst.n_modes):
+                for k in range(inst.K):
+                    xs, ps, prs = O.markov_bids_at(inst, ev[t, m, :, k], s_idx)
+                    n = n_pts[t, m, k]
+                    assert n == len(xs) >= 1
+                    np.testing.assert_array_equal(p_mw[t, m, k, :n], ps)
+                    np.testing.assert_array_equal(price[t, m, k, :n - 1],
+                                                  np.asarray(prs, np.float64).astype(np.float32))
+                    if Dd == 0:
+                        assert np.all(p_mw[t, m, k, :n] <= 0)   # nothing to sell
+                    if Dc == 0:
+                        assert np.all(p_mw[t, m, k, :n] >= 0)   # nothing to buy
+
+
 def test_bids_at_device_pointers_equal_host():
     import torch
     inst = I.random_instance(23, 5, 200, 4, 15, 15, 2, neg_prob=0.3)
