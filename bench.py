@@ -679,6 +679,29 @@ def run_profile_case(name):
                           full.terminal, s0=full.s0)
     elif name == "config2":
         inst = I.config2()
+    elif name == "config5-grad":
+        # forward solve and the occupancy adjoint of the gradient asset
+        inst = I.config5()
+        d = {k: torch.from_numpy(v).to("cuda") for k, v in E.concat_inputs([inst]).items()}
+        V1 = torch.empty(inst.N * inst.K, device="cuda")
+        mu0 = torch.from_numpy(inst.mu0).to("cuda")
+        J = torch.empty(1, dtype=torch.float64, device="cuda")
+        dp = torch.empty(inst.T * inst.K, device="cuda")
+        dt = torch.empty(inst.T * inst.K * inst.K, device="cuda")
+        de = torch.empty(2, dtype=torch.float64, device="cuda")
+        s = E.Solver([inst], device_ptrs=True)
+        s.autotune()
+        for rep in range(2):
+            if rep:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("esdp_profile")
+            s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+            s.grad(0, mu0, J, dp, dt, de)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        print(json.dumps({"profile_case": name, "launch": s.launch_info()}))
+        return
     elif name == "table3-20h":
         # the stagewise-independent path on the 20 h / S = 2001 / P = 203 shape
         prob = I.table3_problem(4)

@@ -18,7 +18,8 @@
 // occ_kernel runs the forward pass over a segment of stages in one
 // cooperative launch (one bounded grid barrier per stage, between the scatter
 // and the contraction); dtrans_kernel then forms dJ/dP for the segment from
-// the stored post-decision occupancies and values.
+// the stored post-decision occupancies and values (a split-row reduction per
+// stage and 32 x 32 output tile).
 #include <cuda_runtime.h>
 
 #include "../../include/esdp.h"
@@ -87,6 +88,10 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
     for (int i = tid; i < K + 5; i += nth) sk[i] = 0.0;
+    {  // P_t for the contraction: its load overlaps the scatter
+      const float* P = p.trans + (size_t)(t - 1) * K * K;
+      for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
+    }
     __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
     const float* price_t = p.price + (size_t)(t - 1) * K;
@@ -142,9 +147,6 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     ++epoch;
     if (!grid_barrier(p.bar, epoch * (int)gridDim.x, p.status, p.timeout_ns, &s_abort)) return;
     // contraction of the post-decision occupancy with P_t (own rows)
-    const float* P = p.trans + (size_t)(t - 1) * K * K;
-    for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
-    __syncthreads();
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const int row = i / K, k2 = i - row * K;
       const float* pr = post + (size_t)row * K;
@@ -156,38 +158,91 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   }
 }
 
-__global__ void dtrans_kernel(const DTransParams p) {
-  const int K = p.K;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ts = blockIdx.y;
-  if (e >= K * K) return;
-  const int k = e / K, k2 = e - k * K;
-  const float* post = p.post + (size_t)ts * p.MN * K;
-  const float* v = p.vnext + (size_t)ts * p.MN * K;
-  // V_{t+1} = V'_{t+1} + c_{t+1}: sum post * V' plus c_{t+1} times the mass
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  float mass[4] = {0.f, 0.f, 0.f, 0.f};
-  int row = 0;
-  for (; row + 4 <= p.MN; row += 4) {
+// dJ/dP_t = post_t^T V_{t+1} over all rows (m, s): one block per (stage,
+// 32 x 32 tile of (k, k2)).  Lane l of every warp owns column k2 = 32 tx + l
+// and keeps the 32 sums of its tile rows k = 32 ty + j in registers; the 16
+// warps take interleaved rows, two per iteration with every load issued
+// before the FMAs (a warp's post values of a row are broadcast reads of four
+// at a time).  The warp partials are added in double in a fixed order (the
+// upper eight warps' first, through shared memory), then c_{t+1} times the
+// occupancy mass of k (V_{t+1} = V'_{t+1} + c_{t+1}).  Deterministic.
+constexpr int kDtWarps = 16;
+__global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParams p) {
+  __shared__ float s_acc[kDtWarps / 2][32][33];
+  __shared__ float s_mass[kDtWarps][32];
+  const int K = p.K, MN = p.MN;
+  const int tiles = (K + 31) / 32;
+  const int ts = blockIdx.y, ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k2 = 32 * tx + lane, kb = 32 * ty;
+  const int nk = min(32, K - kb);
+  const float* post = p.post + (size_t)ts * MN * K;
+  const float* v = p.vnext + (size_t)ts * MN * K;
+  float acc[32];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float w = __ldg(post + (size_t)(row + u) * K + k);
-      if (w != 0.f) {
-        acc[u] = fmaf(w, __ldg(v + (size_t)(row + u) * K + k2), acc[u]);
-        mass[u] += w;
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  float mass = 0.f;
+  const bool vec = (K & 3) == 0 && nk == 32;
+  for (int row = w; row < MN; row += 2 * kDtWarps) {
+    const int rb = row + kDtWarps;
+    const bool two = rb < MN;
+    const float* pa = post + (size_t)row * K + kb;
+    const float* pb = post + (size_t)(two ? rb : row) * K + kb;
+    const float va = k2 < K ? __ldg(v + (size_t)row * K + k2) : 0.f;
+    const float vb = (k2 < K && two) ? __ldg(v + (size_t)rb * K + k2) : 0.f;
+    if (lane < nk) mass += __ldg(pa + lane) + (two ? __ldg(pb + lane) : 0.f);
+    if (vec) {
+      const float4* a4 = reinterpret_cast<const float4*>(pa);
+      const float4* b4 = reinterpret_cast<const float4*>(pb);
+      float4 xa[8], xb[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        xa[q] = __ldg(a4 + q);
+        xb[q] = __ldg(b4 + q);
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        acc[4 * q] = fmaf(xb[q].x, vb, fmaf(xa[q].x, va, acc[4 * q]));
+        acc[4 * q + 1] = fmaf(xb[q].y, vb, fmaf(xa[q].y, va, acc[4 * q + 1]));
+        acc[4 * q + 2] = fmaf(xb[q].z, vb, fmaf(xa[q].z, va, acc[4 * q + 2]));
+        acc[4 * q + 3] = fmaf(xb[q].w, vb, fmaf(xa[q].w, va, acc[4 * q + 3]));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < nk) acc[j] = fmaf(__ldg(pb + j), vb, fmaf(__ldg(pa + j), va, acc[j]));
     }
   }
-  for (; row < p.MN; ++row) {
-    const float w = __ldg(post + (size_t)row * K + k);
-    if (w != 0.f) {
-      acc[0] = fmaf(w, __ldg(v + (size_t)row * K + k2), acc[0]);
-      mass[0] += w;
-    }
+  // fixed-order reduction: upper warps through shared memory into the lower,
+  // then the lower eight in double
+  const int half = kDtWarps / 2;
+  if (w >= half) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) s_acc[w - half][j][lane] = acc[j];
   }
-  const double sv = ((double)acc[0] + (double)acc[1]) + ((double)acc[2] + (double)acc[3]);
-  const double sm = ((double)mass[0] + (double)mass[1]) + ((double)mass[2] + (double)mass[3]);
-  p.d_trans[(size_t)ts * K * K + e] = (float)(sv + p.cnext[ts] * sm);
+  s_mass[w][lane] = mass;
+  __syncthreads();
+  if (w < half) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] += s_acc[w][j][lane];
+  }
+  __syncthreads();
+  if (w < half) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) s_acc[w][j][lane] = acc[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int j = e >> 5, l = e & 31;
+    const int k = kb + j, kk2 = 32 * tx + l;
+    if (k >= K || kk2 >= K) continue;
+    double sv = 0.0, sm = 0.0;
+#pragma unroll
+    for (int q = 0; q < half; ++q) sv += (double)s_acc[q][j][l];
+#pragma unroll
+    for (int q = 0; q < kDtWarps; ++q) sm += (double)s_mass[q][j];
+    p.d_trans[(size_t)ts * K * K + (size_t)k * K + kk2] = (float)(sv + p.cnext[ts] * sm);
+  }
 }
 
 }  // namespace
@@ -206,9 +261,8 @@ cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream
 
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream) {
   if (p.n_t == 0) return cudaSuccess;
-  const int block = 256;
-  dim3 grid((p.K * p.K + block - 1) / block, p.n_t);
-  dtrans_kernel<<<grid, block, 0, stream>>>(p);
+  const int tiles = (p.K + 31) / 32;
+  dtrans_kernel<<<dim3(tiles * tiles, p.n_t), 32 * kDtWarps, 0, stream>>>(p);
   return cudaGetLastError();
 }
 
