@@ -90,6 +90,8 @@ struct esdp_ctx {
   int* d_status = nullptr;
   void* bid_scr = nullptr;        // bid-curve scratch (host-mode outputs, packed form), grown on demand
   size_t bid_scr_bytes = 0;
+  void* grad_scr = nullptr;       // esdp_grad workspace, grown on demand
+  size_t grad_scr_bytes = 0;
   // inputs of the last solve (device pointers)
   const float* last_price = nullptr;
   const float* last_trans = nullptr;
@@ -678,6 +680,7 @@ void esdp_destroy(esdp_ctx* c) {
   for (Plan& p : c->solo) free_plan(&p);
   for (void* p : c->allocs) cudaFree(p);
   cudaFree(c->bid_scr);
+  cudaFree(c->grad_scr);
   delete c;
 }
 
@@ -1048,32 +1051,42 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   if (sp.adev.empty()) {
     if ((rc = plan_default(c, std::vector<int>{asset}, &sp))) return rc;
   }
-  // scratch (freed at the end of the call)
-  std::vector<void*> scratch;
-  auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 4)) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    scratch.push_back(*p);
-    return true;
-  };
-  auto release = [&]() {
-    cudaStreamSynchronize(st);
-    for (void* p : scratch) cudaFree(p);
-  };
+  // workspace: carved from the context's gradient scratch (kept across calls)
   void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
-      *dcost64, *dco;
+      *dcost64, *dco, *opart, *opart_cost;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
-  if (!alloc(&seg_pol, L * C * pb) || !alloc(&seg_v, L * (C + 1) * 4) ||
-      !alloc(&seg_post, L * C * 4) || !alloc(&rho, L * 4) || !alloc(&ev2, 2 * L * 4) ||
-      !alloc(&dprice64, (size_t)T * K * 8) || !alloc(&acc, 8 * 8) || !alloc(&bar, 4) ||
-      !alloc(&d_mu, K * 4) || !alloc(&dJ, 8) || !alloc(&dtr, (size_t)T * K * K * 4) ||
-      !alloc(&dpr, (size_t)T * K * 4) || !alloc(&dcost64, (size_t)a.A * 8) ||
-      !alloc(&dco, (size_t)a.A * 4)) {
-    release();
-    return fail(c, ESDP_ENOMEM, "gradient scratch allocation failed");
+  const int MN = M * N;
+  int ogrid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));  // occupancy CTAs
+  const int orows = (MN + ogrid - 1) / ogrid;
+  ogrid = (MN + orows - 1) / orows;
+  {
+    void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
+                     &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost};
+    const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
+                            (size_t)T * K * 8, 8 * 8, 4, (size_t)K * 4, 8,
+                            (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
+                            (size_t)a.A * 4, (size_t)C * ogrid * (K + 5) * 8,
+                            (size_t)ogrid * a.A * 8};
+    size_t total = 0;
+    for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
+    if (total > c->grad_scr_bytes) {
+      cudaFree(c->grad_scr);  // synchronises: no earlier call still uses it
+      c->grad_scr = nullptr;
+      c->grad_scr_bytes = 0;
+      if (getenv("ESDP_FAIL_ALLOC") || cudaMalloc(&c->grad_scr, total) != cudaSuccess) {
+        cudaGetLastError();
+        c->grad_scr = nullptr;
+        return fail(c, ESDP_ENOMEM, "gradient scratch allocation failed");
+      }
+      c->grad_scr_bytes = total;
+    }
+    char* q = (char*)c->grad_scr;
+    for (int i = 0; i < 16; ++i) {
+      *outs[i] = q;
+      q += (sizes[i] + 255) / 256 * 256;
+    }
   }
+  auto release = [&]() { cudaStreamSynchronize(st); };
   auto cfail = [&](cudaError_t e, const char* what) {
     release();
     return cuda_fail(c, e, what);
@@ -1126,10 +1139,8 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     OccParams op{};
     op.N = N; op.K = K; op.M = M; op.A = a.A; op.D_dis = a.D_dis;
     op.t_lo = t_lo; op.t_hi = t_hi;
-    const int MN = M * N;
-    int grid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));
-    op.grid_rows = (MN + grid - 1) / grid;
-    grid = (MN + op.grid_rows - 1) / op.grid_rows;
+    op.grid_rows = orows;
+    const int grid = ogrid;
     op.delta = a.s_max / (double)(N - 1);
     op.eta_c = a.eta_c;
     op.eta_d = a.eta_d;
@@ -1145,10 +1156,13 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.d_price = (double*)dprice64;
     op.acc = (double*)acc;
     op.d_cost = (double*)dcost64;
+    op.part = (double*)opart;
+    op.part_cost = (double*)opart_cost;
     op.bar = (int*)bar;
     op.status = c->d_status;
     op.timeout_ns = c->timeout_ns;
     if ((e = launch_occupancy(op, grid, 256, st)) != cudaSuccess) return cfail(e, "occupancy");
+    if ((e = launch_occ_reduce(op, grid, st)) != cudaSuccess) return cfail(e, "occupancy sums");
     DTransParams dp{};
     dp.n_t = nt;
     dp.MN = MN;

@@ -210,13 +210,18 @@ struct OccParams {
   float* rho;             // [M][N][K], holds rho_{t_lo} on entry, rho_{t_hi+1} on exit
   float* post;            // [C][M][N][K], zero on entry
   double* d_price;        // [T][K] (accumulated)
-  double* acc;            // [5]: d_eta_c, d_eta_d, J_occ (expected reward), mass, d_switch
+  double* acc;            // [5]: d_eta_c, d_eta_d, (two unused slots), d_switch
   double* d_cost;         // [A] (accumulated)
+  double* part;           // [C][grid][K + 5] per-CTA stage partials (dprice, then acc's five)
+  double* part_cost;      // [grid][A] per-CTA segment partials of d_cost
   int* bar;               // grid barrier counter (zero on entry)
   int* status;
   unsigned long long timeout_ns;
 };
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream);
+// Adds the per-CTA partials of a segment (grid CTAs, stages t_lo..t_hi) to
+// d_price, acc and d_cost, summing in a fixed order.
+cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream);
 
 struct DTransParams {
   int n_t, MN, K;

@@ -71,23 +71,29 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
+  // float32 per-state terms and shared sums (few terms each: this part's FP64
+  // pipe is 64x slower than FP32), double from the per-warp sums on
   extern __shared__ double osm[];
-  double* sk = osm;                                          // [K] dprice partials, then [5]
-  double* sc = osm + p.K + 5;                                // [A] cost partials (segment)
-  float* Ps = reinterpret_cast<float*>(osm + p.K + 5 + p.A);  // [K][K]
+  double* sacc = osm;                                       // [8] warp-sum accumulators
+  float* sk = reinterpret_cast<float*>(osm + 8);            // [K] dprice partials
+  float* sc = sk + p.K;                                     // [A] cost partials (segment)
+  float* Ps = sc + p.A;                                     // [K][K]
   __shared__ int s_abort;
   const int K = p.K, N = p.N, M = p.M, MN = M * N;
   const size_t MNK = (size_t)MN * K;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int r0 = blockIdx.x * p.grid_rows;
   const int r1 = min(MN, r0 + p.grid_rows);
+  // d rho lam delta / eta_c^2 per charging step, d rho lam delta per discharging step
+  const float coef_c = (float)(p.delta / (p.eta_c * p.eta_c)), coef_d = (float)p.delta;
   if (tid == 0) s_abort = 0;
-  for (int a = tid; a < p.A; a += nth) sc[a] = 0.0;
+  for (int a = tid; a < p.A; a += nth) sc[a] = 0.f;
   __syncthreads();
   int epoch = 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
-    for (int i = tid; i < K + 5; i += nth) sk[i] = 0.0;
+    for (int i = tid; i < K; i += nth) sk[i] = 0.f;
+    if (tid < 8) sacc[tid] = 0.0;
     {  // P_t for the contraction: its load overlaps the scatter
       const float* P = p.trans + (size_t)(t - 1) * K * K;
       for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
@@ -95,7 +101,7 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
     const float* price_t = p.price + (size_t)(t - 1) * K;
-    double dc = 0.0, dd = 0.0, jr = 0.0, ms = 0.0, dsw = 0.0;
+    float dc = 0.f, dd = 0.f, dsw = 0.f;
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const float rho = p.rho[i];
       if (rho == 0.f) continue;
@@ -111,39 +117,32 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       }
       const int m2 = (M == 2) ? (d < 0 ? 0 : (d > 0 ? 1 : m)) : 0;
       atomicAdd(post + ((size_t)m2 * N + s + d) * K + k, rho);
-      const double lam = (double)price_t[k];
-      const double e = (double)p.e[a];
-      atomicAdd(&sk[k], (double)rho * e);
-      if (d > 0) dc += (double)rho * lam * ((double)d * p.delta / (p.eta_c * p.eta_c));
-      if (d < 0) dd += (double)rho * lam * (-(double)d * p.delta);
-      double r = lam * e - (double)p.cost[a];
-      atomicAdd(&sc[a], -(double)rho);
-      if (M == 2 && m == 1 && d < 0) {
-        r -= (double)p.sw;
-        dsw -= (double)rho;
-      }
-      jr += (double)rho * r;
-      ms += (double)rho;
+      const float lam = price_t[k];
+      atomicAdd(&sk[k], rho * p.e[a]);
+      if (d > 0) dc = fmaf(rho * lam, (float)d * coef_c, dc);
+      if (d < 0) dd = fmaf(rho * lam, (float)(-d) * coef_d, dd);
+      atomicAdd(&sc[a], -rho);
+      if (M == 2 && m == 1 && d < 0) dsw -= rho;
     }
-    dc = warp_sum(dc);
-    dd = warp_sum(dd);
-    jr = warp_sum(jr);
-    ms = warp_sum(ms);
-    dsw = warp_sum(dsw);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dc += __shfl_xor_sync(0xffffffffu, dc, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      dsw += __shfl_xor_sync(0xffffffffu, dsw, o);
+    }
     if ((tid & 31) == 0) {
-      atomicAdd(&sk[K + 0], dc);
-      atomicAdd(&sk[K + 1], dd);
-      atomicAdd(&sk[K + 2], jr);
-      atomicAdd(&sk[K + 3], ms);
-      atomicAdd(&sk[K + 4], dsw);
+      atomicAdd(&sacc[0], (double)dc);
+      atomicAdd(&sacc[1], (double)dd);
+      atomicAdd(&sacc[4], (double)dsw);
     }
     __syncthreads();
-    for (int k = tid; k < K; k += nth)
-      if (sk[k] != 0.0) atomicAdd(&p.d_price[(size_t)(t - 1) * K + k], sk[k]);
-    if (tid < 5 && sk[K + tid] != 0.0) atomicAdd(&p.acc[tid], sk[K + tid]);
-    if (t == p.t_hi)  // the segment's cost partials, once
+    // this CTA's partials of the stage (and, once, of the segment's costs):
+    // plain stores, added up after the launch in a fixed order
+    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * (K + 5);
+    for (int i = tid; i < K + 5; i += nth) pr[i] = i < K ? (double)sk[i] : sacc[i - K];
+    if (t == p.t_hi)
       for (int a = tid; a < p.A; a += nth)
-        if (sc[a] != 0.0) atomicAdd(&p.d_cost[a], sc[a]);
+        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)sc[a];
     ++epoch;
     if (!grid_barrier(p.bar, epoch * (int)gridDim.x, p.status, p.timeout_ns, &s_abort)) return;
     // contraction of the post-decision occupancy with P_t (own rows)
@@ -245,11 +244,48 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
   }
 }
 
+// Per-CTA partials of one segment into the accumulated gradients, one warp
+// per output: (stage, state) -> d_price, the five accumulators, actions ->
+// d_cost.  Lane l adds the partials l, l + 32, ... in order, then a fixed
+// butterfly over the lanes: the same sum on every run.
+__global__ void occ_reduce_kernel(const OccParams p, int grid) {
+  const int K = p.K, n_t = p.t_hi - p.t_lo + 1;
+  const int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_price = n_t * K;
+  if (o >= n_price + 5 + p.A) return;  // whole warps
+  double s = 0.0;
+  if (o < n_price) {
+    const int ts = o / K, k = o - ts * K;
+    for (int b = lane; b < grid; b += 32) s += p.part[((size_t)ts * grid + b) * (K + 5) + k];
+  } else if (o < n_price + 5) {
+    const int q = o - n_price;
+    for (int i = lane; i < n_t * grid; i += 32) s += p.part[(size_t)i * (K + 5) + K + q];
+  } else {
+    const int a = o - n_price - 5;
+    for (int b = lane; b < grid; b += 32) s += p.part_cost[(size_t)b * p.A + a];
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (o < n_price)
+      p.d_price[(size_t)(p.t_lo - 1 + o / K) * K + o % K] += s;
+    else if (o < n_price + 5)
+      p.acc[o - n_price] += s;
+    else
+      p.d_cost[o - n_price - 5] += s;
+  }
+}
+
 }  // namespace
 
+cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream) {
+  const int n = (p.t_hi - p.t_lo + 1) * p.K + 5 + p.A;  // outputs, one warp each
+  occ_reduce_kernel<<<(n + 7) / 8, 256, 0, stream>>>(p, grid);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream) {
-  const size_t smem =
-      (size_t)(p.K + 5 + p.A) * sizeof(double) + (size_t)p.K * p.K * sizeof(float);
+  const size_t smem = 8 * sizeof(double) + (size_t)(p.K + p.A + p.K * p.K) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(occ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
