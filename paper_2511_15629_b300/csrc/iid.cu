@@ -302,9 +302,11 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
 
 // ---- bid curves (eq. 8-11) and market clearing on the kept values
 
-struct IidActions {  // per action, in double
+struct IidActions {  // per action
   const double* p;   // power level (MW)
   const double* f;   // SoC shift in grid steps F(p) tau / delta
+  const float* ptf;  // float(p tau): energy sold (MWh), for the float32 filter
+  const float* ff;   // float(f)
   int P, S;
   double tau;
 };
@@ -368,6 +370,55 @@ __global__ void iid_bids_kernel(const IidActions A, const float* v_all, int t0, 
 // lam_t p tau accrues.  One warp per price path: the lanes take the actions
 // in turn and the warp reduces (larger value, on equal values the smaller
 // action index).
+// Float32 enclosure of the clearing value lam p tau + V_t(z + f_a) of action
+// a: 0 = surely infeasible, 1 = surely feasible with the value in [lo, hi],
+// 2 = feasibility undecided.  The float position zn = z + f carries an error
+// of at most m = 2^-24 (|z| + |f| + |zn|) grid steps; within m of a grid
+// point the double evaluation may snap or interpolate towards either
+// neighbour, elsewhere it interpolates on the same two points with a weight
+// within m of the float one; the float arithmetic adds a few roundings of the
+// magnitudes involved.
+__device__ __forceinline__ int clear_bounds(const IidActions& A, const float* v, float zf,
+                                            float lf, int a, float& lo, float& hi) {
+  const float U = 5.97e-8f;  // 2^-24, slightly rounded up
+  const float ff = A.ff[a];
+  const float zn = zf + ff;
+  const float m = U * (fabsf(zf) + fabsf(ff) + fabsf(zn)) + 1e-7f;
+  const float top = (float)(A.S - 1);
+  if (zn < -m - 1e-6f || zn > top + m + 1e-6f) return 0;
+  if (zn < m + 1e-6f || zn > top - m - 1e-6f) return 2;
+  float vf, ev, mag;
+  const float jr = rintf(zn);
+  if (fabsf(zn - jr) <= m) {
+    const int j = (int)jr;  // in [0, S-1]
+    const float vj = v[j];
+    const float dl = j > 0 ? fabsf(vj - v[j - 1]) : 0.f;
+    const float dr = j < A.S - 1 ? fabsf(v[j + 1] - vj) : 0.f;
+    vf = vj;
+    ev = 2.01f * m * fmaxf(dl, dr) * 1.01f;
+    mag = fabsf(vj);
+  } else {
+    const int j = (int)floorf(zn);  // in [0, S-2], zn - j in (m, 1 - m)
+    const float b = zn - (float)j;
+    const float v0 = v[j], v1 = v[j + 1];
+    vf = (1.f - b) * v0 + b * v1;
+    ev = 1.01f * (m + 1e-9f) * fabsf(v1 - v0);
+    mag = fabsf(v0) + fabsf(v1);
+  }
+  const float pr = lf * A.ptf[a];
+  const float val = pr + vf;
+  const float err = 1.01f * (ev + U * (6.f * mag + 4.f * fabsf(pr) + 2.f * fabsf(val))) + 1e-30f;
+  lo = val - err;
+  hi = val + err;
+  return 1;
+}
+
+// One warp per price path through all stages: at each stage the cleared
+// action maximises lam_t p tau + V_t(z + f_a) over the feasible actions (the
+// larger value, then the smaller index), exactly as in double.  A float32 pass
+// first encloses every action's value; its best lower bound L over the surely
+// feasible actions lies below the maximum, so only the actions whose upper
+// bound reaches L (or whose feasibility is undecided) are evaluated in double.
 __global__ void iid_clear_kernel(const IidActions A, const float* v_all, int T, const float* lam,
                                  int n_paths, double s0, double* revenue, double* s_end,
                                  int* actions) {
@@ -377,10 +428,22 @@ __global__ void iid_clear_kernel(const IidActions A, const float* v_all, int T, 
   double z = s0, rev = 0.0;
   for (int t = 1; t <= T; ++t) {
     const float* v = v_all + (size_t)t * A.S;
-    const double l = (double)lam[(size_t)path * T + t - 1];
+    const float lf = lam[(size_t)path * T + t - 1];
+    const double l = (double)lf;
+    const float zf = (float)z;
+    float L = -INFINITY;
+    for (int a = lane; a < A.P; a += 32) {
+      float lo, hi;
+      if (clear_bounds(A, v, zf, lf, a, lo, hi) == 1) L = fmaxf(L, lo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) L = fmaxf(L, __shfl_xor_sync(0xffffffffu, L, o));
     double best = -INFINITY;
     int arg = 0x7fffffff;
     for (int a = lane; a < A.P; a += 32) {
+      float lo, hi;
+      const int kind = clear_bounds(A, v, zf, lf, a, lo, hi);
+      if (kind == 0 || (kind == 1 && hi < L)) continue;
       const double zn = __dadd_rn(z, A.f[a]);
       if (!feasible(zn, A.S)) continue;
       const double val = __dadd_rn(__dmul_rn(l, __dmul_rn(A.p[a], A.tau)), v_at(v, A.S, zn));
@@ -647,22 +710,28 @@ int make_actions(const esdp_iid_problem& q, ActionsBuf* out, char* err, int32_t 
   const std::vector<double> p = action_grid(q);
   const int P = (int)p.size();
   const double delta = q.s_max / (double)(q.S - 1);
-  std::vector<double> h(2 * P);
+  // [p (double)][f (double)][float(p tau), float(f) as float pairs in P doubles]
+  std::vector<double> h(3 * P);
+  float* hf = reinterpret_cast<float*>(h.data() + 2 * P);
   for (int a = 0; a < P; ++a) {
     h[a] = p[a];
     const double F = p[a] >= 0 ? -p[a] / q.eta : -q.eta * p[a];
     h[P + a] = F * q.tau / delta;
+    hf[a] = (float)(p[a] * q.tau);
+    hf[P + a] = (float)h[P + a];
   }
-  if (cudaMalloc(&out->d, 2 * P * sizeof(double)) != cudaSuccess) {
+  if (cudaMalloc(&out->d, 3 * P * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return msg(err, err_len, ESDP_ENOMEM, "allocation failed");
   }
-  if (cudaMemcpy(out->d, h.data(), 2 * P * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(out->d, h.data(), 3 * P * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(out->d);
     return msg(err, err_len, ESDP_ECUDA, "copy failed");
   }
   out->a.p = out->d;
   out->a.f = out->d + P;
+  out->a.ptf = reinterpret_cast<const float*>(out->d + 2 * P);
+  out->a.ff = out->a.ptf + P;
   out->a.P = P;
   out->a.S = q.S;
   out->a.tau = q.tau;

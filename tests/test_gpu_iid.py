@@ -174,6 +174,39 @@ def test_iid_clearing_matches_oracle():
         assert s_end[i] == pytest.approx(z, abs=1e-9)
 
 
+@pytest.mark.parametrize("case", ["endpoints", "ties"])
+def test_iid_clearing_exact_on_hard_paths(case):
+    """The float32 enclosure in the clearing kernel must never change a
+    decision: 64 paths with fractional end-point shifts and prices swinging
+    from -60 to 150 (the SoC reaches both ends of the grid), and a case where
+    every action ties (zero prices, zero values: the smallest feasible index
+    is cleared at every stage)."""
+    import torch
+    prob = I.iid_problem(16, 30, 61, 5, 3.0, p_max=1.3, neg_prob=0.3)
+    if case == "endpoints":
+        _, V_all = _device_values(prob)
+        rng = np.random.default_rng(23)
+        lam = rng.uniform(-60.0, 150.0, size=(64, prob.T)).astype(np.float32)
+        s0 = 1.5
+    else:
+        V_all = torch.zeros((prob.T + 1, prob.S), device="cuda")
+        lam = np.zeros((8, prob.T), np.float32)
+        s0 = 0.0
+    rev, s_end, act = E.iid_clear(prob, V_all, torch.from_numpy(lam).cuda(), s0)
+    rev, s_end, act = rev.cpu().numpy(), s_end.cpu().numpy(), act.cpu().numpy()
+    V = V_all.cpu().numpy()
+    ends = 0
+    for i in range(lam.shape[0]):
+        r, z, a = O.paper_clear(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau, V, lam[i], s0)
+        np.testing.assert_array_equal(act[i], a)
+        assert rev[i] == pytest.approx(r, rel=1e-12, abs=1e-9)
+        assert s_end[i] == pytest.approx(z, abs=1e-9)
+    if case == "endpoints":
+        p, f = O._shifts(prob.S, prob.s_max, prob.p_max, prob.eta, prob.tau)
+        assert any(abs(x - round(x)) > 1e-6 for x in f)   # fractional end-point shifts
+        assert (act == 0).any() and (act == len(p) - 1).any()
+
+
 def test_iid_clearing_monte_carlo_reproduces_value():
     """Price paths drawn from the model's own samples (eta = 1: every action
     on the grid): the mean cleared revenue is V_0(s0) within 3 standard
