@@ -402,14 +402,19 @@ int upload_plan(esdp_ctx* c, Plan* p, cudaStream_t st) {
   return ESDP_OK;
 }
 
+// prep = false: the row sums and the prepared P of the plan's assets are
+// already in place (a gradient re-sweep of the last solve's inputs).
+// d_assets: the plan's asset descriptors on the device, when not the plan's
+// own uploaded copy (the gradient's per-segment descriptors).
 int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const float* cost,
-             const float* terminal, float* v1, cudaStream_t st) {
+             const float* terminal, float* v1, cudaStream_t st, bool prep = true,
+             const AssetDev* d_assets = nullptr) {
   if (!p->uploaded) {
     int rc = upload_plan(c, p, st);
     if (rc) return rc;
   }
   SweepParams sp{};
-  sp.assets = p->d_assets;
+  sp.assets = d_assets ? d_assets : p->d_assets;
   sp.items = p->d_items;
   sp.cta_items = p->d_cta;
   sp.price = price;
@@ -435,7 +440,8 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
   sp.tmem_cols = p->tmem_cols;
   CK(cudaMemsetAsync(p->d_flags, 0, std::max(1, p->n_flags) * sizeof(int), st), "reset flags");
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "reset status");
-  CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
+  if (prep)
+    CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
   CK(launch_sweep(p->shape, sp, st), "sweep launch");
   return ESDP_OK;
 }
@@ -1053,7 +1059,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   }
   // workspace: carved from the context's gradient scratch (kept across calls)
   void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
-      *dcost64, *dco, *opart, *opart_cost;
+      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
   const int MN = M * N;
   int ogrid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));  // occupancy CTAs
@@ -1061,12 +1067,14 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   ogrid = (MN + orows - 1) / orows;
   {
     void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
-                     &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost};
+                     &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
+                     &opart_acc, &dsegs};
     const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
                             (size_t)T * K * 8, 8 * 8, 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
-                            (size_t)a.A * 4, (size_t)C * ogrid * (K + 5) * 8,
-                            (size_t)ogrid * a.A * 8};
+                            (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
+                            (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
+                            (size_t)nseg * sizeof(AssetDev)};
     size_t total = 0;
     for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
     if (total > c->grad_scr_bytes) {
@@ -1081,7 +1089,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
       c->grad_scr_bytes = total;
     }
     char* q = (char*)c->grad_scr;
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 18; ++i) {
       *outs[i] = q;
       q += (sizes[i] + 255) / 256 * 256;
     }
@@ -1106,10 +1114,12 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   const float* trans = c->last_trans + c->off_trans[asset];
   const float* cost = c->last_cost + c->off_cost[asset];
   const float* terminal = c->last_terminal + c->off_terminal[asset];
+  // the re-sweeps' asset descriptors, one per segment, uploaded together (a
+  // host upload per segment would drain the stream before each re-sweep)
+  std::vector<AssetDev> segs(nseg, sp.adev[0]);
   for (int j = 0; j < nseg; ++j) {
     const int t_lo = 1 + j * C, t_hi = std::min(T, (j + 1) * C);
-    const int nt = t_hi - t_lo + 1;
-    AssetDev& d = sp.adev[0];
+    AssetDev& d = segs[j];
     d.t_hi = t_hi;
     d.t_lo = t_lo;
     d.v_start = (t_hi == T) ? nullptr : c->d_ckpt[asset] + (size_t)j * L;
@@ -1122,15 +1132,28 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     d.ckpt_every = 0;
     d.ckpt = nullptr;
     d.v_keep = (float*)seg_v;
+  }
+  if (!sp.uploaded) {  // work items and CTA lists, once per context
+    if ((rc = upload_plan(c, &sp, st))) {
+      release();
+      return rc;
+    }
+  }
+  if ((e = cudaMemcpyAsync(dsegs, segs.data(), (size_t)nseg * sizeof(AssetDev),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cfail(e, "segment descriptors");
+  for (int j = 0; j < nseg; ++j) {
+    const int t_lo = 1 + j * C, t_hi = std::min(T, (j + 1) * C);
+    const int nt = t_hi - t_lo + 1;
     sp.n_steps = nt;
-    sp.uploaded = false;
+    // the last solve prepared the row sums and P of these transition matrices
     if ((rc = run_plan(c, &sp, c->last_price, c->last_trans, c->last_cost, c->last_terminal,
-                       nullptr, st))) {
+                       nullptr, st, false, (const AssetDev*)dsegs + j))) {
       release();
       return rc;
     }
     // V_{t_hi+1} after the segment's values, so V_{t+1} of stage t sits at t - t_lo + 1
-    const float* vend = d.v_start ? d.v_start : terminal;
+    const float* vend = segs[j].v_start ? segs[j].v_start : terminal;
     if ((e = cudaMemcpyAsync((float*)seg_v + (size_t)nt * L, vend, L * 4, cudaMemcpyDeviceToDevice,
                              st)) != cudaSuccess)
       return cfail(e, "segment copy");
@@ -1158,6 +1181,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.d_cost = (double*)dcost64;
     op.part = (double*)opart;
     op.part_cost = (double*)opart_cost;
+    op.part_acc = (double*)opart_acc;
     op.bar = (int*)bar;
     op.status = c->d_status;
     op.timeout_ns = c->timeout_ns;

@@ -212,8 +212,9 @@ struct OccParams {
   double* d_price;        // [T][K] (accumulated)
   double* acc;            // [5]: d_eta_c, d_eta_d, (two unused slots), d_switch
   double* d_cost;         // [A] (accumulated)
-  double* part;           // [C][grid][K + 5] per-CTA stage partials (dprice, then acc's five)
+  double* part;           // [C][grid][K] per-CTA stage partials of dprice
   double* part_cost;      // [grid][A] per-CTA segment partials of d_cost
+  double* part_acc;       // [grid][8] per-CTA segment partials of acc
   int* bar;               // grid barrier counter (zero on entry)
   int* status;
   unsigned long long timeout_ns;

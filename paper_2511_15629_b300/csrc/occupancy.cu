@@ -88,12 +88,12 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   const float coef_c = (float)(p.delta / (p.eta_c * p.eta_c)), coef_d = (float)p.delta;
   if (tid == 0) s_abort = 0;
   for (int a = tid; a < p.A; a += nth) sc[a] = 0.f;
+  if (tid < 8) sacc[tid] = 0.0;  // summed over the segment
   __syncthreads();
   int epoch = 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
     for (int i = tid; i < K; i += nth) sk[i] = 0.f;
-    if (tid < 8) sacc[tid] = 0.0;
     {  // P_t for the contraction: its load overlaps the scatter
       const float* P = p.trans + (size_t)(t - 1) * K * K;
       for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
@@ -136,13 +136,16 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       atomicAdd(&sacc[4], (double)dsw);
     }
     __syncthreads();
-    // this CTA's partials of the stage (and, once, of the segment's costs):
-    // plain stores, added up after the launch in a fixed order
-    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * (K + 5);
-    for (int i = tid; i < K + 5; i += nth) pr[i] = i < K ? (double)sk[i] : sacc[i - K];
-    if (t == p.t_hi)
+    // this CTA's partials of the stage (and, once, of the segment's costs
+    // and accumulators): plain stores, added up after the launch in a fixed
+    // order
+    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
+    for (int i = tid; i < K; i += nth) pr[i] = (double)sk[i];
+    if (t == p.t_hi) {
       for (int a = tid; a < p.A; a += nth)
         p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)sc[a];
+      if (tid < 8) p.part_acc[(size_t)blockIdx.x * 8 + tid] = sacc[tid];
+    }
     ++epoch;
     if (!grid_barrier(p.bar, epoch * (int)gridDim.x, p.status, p.timeout_ns, &s_abort)) return;
     // contraction of the post-decision occupancy with P_t (own rows)
@@ -257,10 +260,10 @@ __global__ void occ_reduce_kernel(const OccParams p, int grid) {
   double s = 0.0;
   if (o < n_price) {
     const int ts = o / K, k = o - ts * K;
-    for (int b = lane; b < grid; b += 32) s += p.part[((size_t)ts * grid + b) * (K + 5) + k];
+    for (int b = lane; b < grid; b += 32) s += p.part[((size_t)ts * grid + b) * K + k];
   } else if (o < n_price + 5) {
     const int q = o - n_price;
-    for (int i = lane; i < n_t * grid; i += 32) s += p.part[(size_t)i * (K + 5) + K + q];
+    for (int b = lane; b < grid; b += 32) s += p.part_acc[(size_t)b * 8 + q];
   } else {
     const int a = o - n_price - 5;
     for (int b = lane; b < grid; b += 32) s += p.part_cost[(size_t)b * p.A + a];
