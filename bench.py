@@ -25,6 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Bellman evals/s (T*N*K*A / sweep s)"
+WORKLOAD = "config2: T=288 N=1001 K=20 A=201 modes=2, sweep + bid curves of every (t,m,k)"
 UNIT = "evals/s"
 
 
@@ -199,8 +200,8 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "config2: T=288 N=1001 K=20 A=201 modes=2 + bid curves",
-                   "parallelism": "cpu"},
+        "config": {"workload": WORKLOAD, "evals_per_step": inst.evals,
+                   "parallelism": f"cpu ({cores} threads)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full steps (solve + envelopes)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -371,8 +372,7 @@ def run_esdp(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "config2: T=288 N=1001 K=20 A=201 modes=2, sweep + bid "
-                                   "curves of every (t,m,k)",
+            "config": {"workload": WORKLOAD,
                        "evals_per_step": inst.evals, "l2": "flushed between steps (512 MB)",
                        "parallelism": f"replicas x{world}", "launch": info},
             "sweep_ms": t_sweep / args.steps * 1e3, "bid_curves_ms": t_hull / args.steps * 1e3,
