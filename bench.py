@@ -541,7 +541,8 @@ def bench_config5(torch, E, I, stream, flush, args, n_sm, f_max):
     s.close()
     return {"plain_ms": t_plain / n * 1e3, "forward_plus_adjoint_ms": t_adj / n * 1e3,
             "adjoint_over_plain": t_adj / t_plain,
-            "plain_evals_per_s": inst.evals * n / t_plain}
+            "plain_evals_per_s": inst.evals * n / t_plain,
+            "plain_frac_alu": inst.evals * n / t_plain / alu_peak_evals(n_sm, f_max)}
 
 
 # The paper's own runtime study (Table III): seconds on an L40S GPU (CuPy)
