@@ -127,22 +127,42 @@ __device__ __forceinline__ bool below_chord(float yi, float yj, float yl, float 
 //
 // kStaged: a block of nw warps first copies the columns of its nw envelopes
 // into shared memory (cp.async; consecutive threads read consecutive price
-// states of one SoC row); each lane's stack then keeps the SoC index (as an
-// exact float) and, in place of the column, the value of its vertices, so a
-// pop or a walk step needs no dependent lookup.  N * 8 bytes per warp.  For
-// grids too long for that, the values are read in place and the slope row
-// holds the stacks' indices.
+// states of one SoC row); each lane's stack then keeps the SoC index (16
+// bits) and, in place of the column, the value of its vertices, so a pop or a
+// walk step needs no dependent lookup.  N * 6 bytes per warp (four blocks of
+// eight warps per SM at N = 1001).  For grids too long for that, the values
+// are read in place and the slope row holds the stacks' indices as floats.
 constexpr int kHullWarps = 8;
 constexpr int kHullSmemBudget = 96 * 1024;  // dynamic shared memory per block
 
+// SoC index (< 2^16) stored in 16 bits -> exact float32, without a
+// conversion instruction: 2^23 + i has i as its low mantissa bits
+__device__ __forceinline__ float index_float(unsigned short i) {
+  return __fsub_rn(__uint_as_float(0x4B000000u + (unsigned)i), 8388608.f);
+}
+
 template <bool kStaged>
 struct HullView {
-  const float* y;   // in place: the envelope's column, stride K
-  float* sv;        // staged: the column, overwritten by the stacks' values
-  float* st;        // stacks' SoC indices (lane l from position l*c)
+  const float* y;          // in place: the envelope's column, stride K
+  float* sv;               // staged: the column, overwritten by the stacks' values
+  unsigned short* st16;    // staged: the stacks' SoC indices (lane l from position l*c)
+  float* st;               // in place: the same as exact floats, in the slope row
   int K;
-  int* lo;          // [32] kept range [lo, hi) of each lane's stack
+  int* lo;                 // [32] kept range [lo, hi) of each lane's stack
   int* hi;
+  // SoC index of the stack entry at position pos, as an exact float
+  __device__ __forceinline__ float xs(int pos) const {
+    if constexpr (kStaged)
+      return index_float(st16[pos]);
+    else
+      return st[pos];
+  }
+  __device__ __forceinline__ void push(int pos, int l, float xl) {
+    if constexpr (kStaged)
+      st16[pos] = (unsigned short)l;
+    else
+      st[pos] = xl;
+  }
   // value of SoC point l before the local hulls
   __device__ __forceinline__ float point(int l) const {
     if constexpr (kStaged)
@@ -156,6 +176,13 @@ struct HullView {
       return sv[pos];
     else
       return __ldg(y + (size_t)(int)st[pos] * K);
+  }
+  // SoC index of the stack entry at position pos
+  __device__ __forceinline__ int xi(int pos) const {
+    if constexpr (kStaged)
+      return st16[pos];
+    else
+      return (int)st[pos];
   }
   // previous kept vertex of (l, i) within lanes >= lmin, or l = -1
   __device__ __forceinline__ void prev(int& l, int& i, int lmin) const {
@@ -196,7 +223,7 @@ __device__ __forceinline__ float hull_slope(float xa, float ya, float xb, float 
 // blockDim.x = 32 << lg_nw
 template <bool kStaged>
 __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams p, int lg_nw) {
-  extern __shared__ float hull_smem[];  // staged: [nw][N] values, then [nw][N] indices
+  extern __shared__ float hull_smem[];  // staged: [nw][N] values, then [nw][N] 16-bit indices
   __shared__ int s_lo[kHullWarps][32], s_hi[kHullWarps][32], s_pre[kHullWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nw = 1 << lg_nw;
@@ -229,10 +256,12 @@ __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams 
   if constexpr (kStaged) {
     v.y = nullptr;
     v.sv = hull_smem + w * N;
-    v.st = hull_smem + (nw + w) * N;
+    v.st16 = reinterpret_cast<unsigned short*>(hull_smem + nw * N) + w * N;
+    v.st = nullptr;
   } else {
     v.y = p.ev + (size_t)tm * N * K + k;
     v.sv = nullptr;
+    v.st16 = nullptr;
     v.st = sl;  // scratch until the slopes
   }
   const int c = ((N + 31) / 32) | 1;
@@ -249,11 +278,11 @@ __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams 
       xj = xi;
       yj = yi;
       if (nh >= 2) {
-        xi = v.st[l0 + nh - 2];
+        xi = v.xs(l0 + nh - 2);
         yi = v.val(l0 + nh - 2);
       }
     }
-    v.st[l0 + nh] = xl;
+    v.push(l0 + nh, l, xl);
     if constexpr (kStaged) v.sv[l0 + nh] = yl;  // position <= l: already read
     ++nh;
     if (nh == 1) {
@@ -289,15 +318,15 @@ __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams 
           break;
         }
       if (la >= 0 && lb >= 0) {
-        float xa = v.st[la * c + ia], ya = v.val(la * c + ia);
-        float xb = v.st[lb * c + ib], yb = v.val(lb * c + ib);
+        float xa = v.xs(la * c + ia), ya = v.val(la * c + ia);
+        float xb = v.xs(lb * c + ib), yb = v.val(lb * c + ib);
         for (bool moved = true; moved;) {
           moved = false;
           for (;;) {  // left end point on or below the chord (its predecessor, right end)?
             int lp = la, ip = ia;
             v.prev(lp, ip, gl);
             if (lp < 0) break;
-            const float xp = v.st[lp * c + ip], yp = v.val(lp * c + ip);
+            const float xp = v.xs(lp * c + ip), yp = v.val(lp * c + ip);
             if (!below_chord(yp, ya, yb, xp, xa, xb)) break;
             la = lp;
             ia = ip;
@@ -309,7 +338,7 @@ __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams 
             int ln = lb, in = ib;
             v.next(ln, in, ge);
             if (ln < 0) break;
-            const float xn = v.st[ln * c + in], yn = v.val(ln * c + in);
+            const float xn = v.xs(ln * c + in), yn = v.val(ln * c + in);
             if (!below_chord(ya, yb, yn, xa, xb, xn)) break;
             lb = ln;
             ib = in;
@@ -351,15 +380,15 @@ __global__ void __launch_bounds__(32 * kHullWarps) hull_kernel(const HullParams 
   if constexpr (kStaged) {
     for (int q = lane; q < total; q += 32) {
       const int pa = position(q);
-      const float xa = v.st[pa];
-      row[q] = (int)xa;
+      const float xa = v.xs(pa);
+      row[q] = v.xi(pa);
       if (q + 1 < total) {
         const int pb = position(q + 1);
-        sl[q] = hull_slope(xa, v.sv[pa], v.st[pb], v.sv[pb], p.delta);
+        sl[q] = hull_slope(xa, v.sv[pa], v.xs(pb), v.sv[pb], p.delta);
       }
     }
   } else {
-    for (int q = lane; q < total; q += 32) row[q] = (int)v.st[position(q)];
+    for (int q = lane; q < total; q += 32) row[q] = v.xi(position(q));
     __syncwarp();  // the slope row held the stacks
     for (int q = lane; q + 1 < total; q += 32) {
       const int a = row[q], b = row[q + 1];
@@ -476,10 +505,10 @@ __global__ void pack_kernel(const int* n_bp, const int* idx, const float* slope,
 cudaError_t launch_hull(const HullParams& p, cudaStream_t stream) {
   const int n_h = p.n_t * p.M * p.K;
   if (n_h == 0) return cudaSuccess;
-  const size_t per_warp = (size_t)p.N * 8;  // staged values and local hulls
+  const size_t per_warp = (size_t)p.N * 6;  // staged values and 16-bit stack indices
   int lg = 3;
   while (lg > 0 && (per_warp << lg) > (size_t)kHullSmemBudget) --lg;
-  if ((per_warp << lg) <= (size_t)kHullSmemBudget) {
+  if (p.N <= 65536 && (per_warp << lg) <= (size_t)kHullSmemBudget) {
     const int nw = 1 << lg, smem = (int)(per_warp << lg);
     cudaError_t e = cudaFuncSetAttribute(hull_kernel<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
