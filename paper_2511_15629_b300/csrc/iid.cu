@@ -14,7 +14,8 @@
 // a tile of SoC rows stages a single column of V_t (its rows plus the action
 // halo), forms the feasible, interpolated next values once per (row, action),
 // and every price sample of the row reuses them; a thread owns one row and
-// kIidKG samples and runs the max over all actions for them.
+// KG samples (8 or 10, whichever needs fewer passes of the block over the
+// tile's rows for its work) and runs the max over all actions for them.
 //
 // Persistent cooperative launch over all stages; tiles synchronise with their
 // neighbours only (release/acquire flags, bounded waits) as in the main sweep.
@@ -36,7 +37,7 @@ namespace esdp {
 namespace {
 
 constexpr int kIidBlock = 512;
-constexpr int kIidKG = 8;  // price samples per thread
+constexpr int kIidKG = 8;  // price samples per thread (the smaller choice)
 constexpr size_t kIidSmemLimit = 227 * 1024;
 
 struct IidParams {
@@ -141,7 +142,7 @@ __device__ bool iid_wait(const IidParams& p, int tile, int need, int t, float* s
   return *(volatile int*)s_abort == 0;
 }
 
-template <bool kPol>
+template <bool kPol, int KG>
 __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
   extern __shared__ float4 ism4[];
   float* ism = reinterpret_cast<float*>(ism4);
@@ -212,14 +213,14 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
         BP[rr * Pp + a] = make_float2(b, pa);
       }
       __syncthreads();
-      // 3. max over the actions for kIidKG price samples of one row; the
+      // 3. max over the actions for KG price samples of one row; the
       //    smallest maximising action index (strict >)
       for (int rr = my_row; my_row < rows_pass && rr < Wt; rr += rows_pass) {
-        const int k0 = my_group * kIidKG;
-        float lam[kIidKG], best[kIidKG];
-        int arg[kIidKG];
+        const int k0 = my_group * KG;
+        float lam[KG], best[KG];
+        int arg[KG];
 #pragma unroll
-        for (int j = 0; j < kIidKG; ++j) {
+        for (int j = 0; j < KG; ++j) {
           lam[j] = k0 + j < R ? __ldg(lam_t + k0 + j) : 0.f;
           best[j] = NEG;
           arg[j] = -1;
@@ -230,9 +231,9 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
           // each packed FMA forms two samples' candidates of one action (two
           // round-to-nearest FMAs, the same values as scalar fmaf)
           const float4* B4 = reinterpret_cast<const float4*>(Br);
-          unsigned long long lam2[kIidKG / 2];
+          unsigned long long lam2[KG / 2];
 #pragma unroll
-          for (int j = 0; j < kIidKG / 2; ++j) lam2[j] = pack2(lam[2 * j], lam[2 * j + 1]);
+          for (int j = 0; j < KG / 2; ++j) lam2[j] = pack2(lam[2 * j], lam[2 * j + 1]);
 #pragma unroll 2
           for (int q = 0; q < (Pp >> 1); q += 2) {
             const float4 x = B4[q], y = B4[q + 1];
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
             const unsigned long long b2 = pack2(y.x, y.x), p2 = pack2(y.y, y.y);
             const unsigned long long b3 = pack2(y.z, y.z), p3 = pack2(y.w, y.w);
 #pragma unroll
-            for (int j = 0; j < kIidKG / 2; ++j) {
+            for (int j = 0; j < KG / 2; ++j) {
               const float2 c0 = fma2u(lam2[j], p0, b0), c1 = fma2u(lam2[j], p1, b1);
               const float2 c2 = fma2u(lam2[j], p2, b2), c3 = fma2u(lam2[j], p3, b3);
               best[2 * j] = max3f(best[2 * j], c0.x, c1.x);
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
           for (int a = 0; a < P; ++a) {
             const float2 bp = Br[a];
 #pragma unroll
-            for (int j = 0; j < kIidKG; ++j) {
+            for (int j = 0; j < KG; ++j) {
               const float v = fmaf(lam[j], bp.y, bp.x);
               if (v > best[j]) {
                 best[j] = v;
@@ -265,13 +266,13 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
         }
         float part = 0.f;
 #pragma unroll
-        for (int j = 0; j < kIidKG; ++j)
+        for (int j = 0; j < KG; ++j)
           if (k0 + j < R) part = fmaf(__ldg(pi_t + k0 + j), best[j], part);
         red[rr * groups + my_group] = part;
         if (kPol) {
           const size_t base = ((size_t)(t - 1) * S + s0 + rr) * R + k0;
 #pragma unroll
-          for (int j = 0; j < kIidKG; ++j) {
+          for (int j = 0; j < KG; ++j) {
             if (k0 + j >= R) break;
             if (p.pol32) p.pol32[base + j] = arg[j];
             if (p.pol16) p.pol16[base + j] = (short)arg[j];
@@ -565,7 +566,7 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     dmin = std::min(dmin, dlo[a]);
     dmax = std::max(dmax, dlo[a] + (fr > 0 ? 1 : 0));
   }
-  const int groups = (R + kIidKG - 1) / kIidKG;
+  const int groups8 = (R + kIidKG - 1) / kIidKG;  // the larger group count (shared memory)
   int dev_id = 0, n_sm = 0;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev_id);
@@ -577,7 +578,7 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     auto al = [](size_t x) { return (x + 31) / 32 * 32; };
     const size_t span = (size_t)w + (size_t)(dmax - dmin) + 2;
     const size_t Pp = (size_t)(P + 3) / 4 * 4;
-    return (al(span) + 2 * (size_t)w * Pp + al(P) + al((size_t)w * groups)) * sizeof(float);
+    return (al(span) + 2 * (size_t)w * Pp + al(P) + al((size_t)w * groups8)) * sizeof(float);
   };
   while (W > 1 && smem_of(W) > kIidSmemLimit) --W;
   if (smem_of(W) > kIidSmemLimit)
@@ -629,8 +630,19 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     ok = h2d(d_lam, lam_hat, (size_t)T * R * 4) && h2d(d_pi, pi_hat, (size_t)T * R * 4) &&
          (!terminal || h2d(d_term, terminal, (size_t)S * 4));
   }
+  // samples per thread: the block takes rows in passes of kIidBlock / groups
+  // rows; of 8 and 10 samples the one with less work per thread for a tile
+  // (passes x samples) wins, 8 on ties
+  auto work = [&](int kg) {
+    const int g = (R + kg - 1) / kg, rows_pass = kIidBlock / g;
+    return rows_pass < 1 ? 1 << 30 : ((W + rows_pass - 1) / rows_pass) * kg;
+  };
+  const int KG = work(10) < work(8) ? 10 : 8;
+  const int groups = (R + KG - 1) / KG;
   // launch shape: one CTA per SM at most, contiguous tile ranges
-  auto fn = policy && q->policy_bytes ? iid_kernel<true> : iid_kernel<false>;
+  const bool pk = policy && q->policy_bytes;
+  auto fn = KG == 10 ? (pk ? iid_kernel<true, 10> : iid_kernel<false, 10>)
+                     : (pk ? iid_kernel<true, 8> : iid_kernel<false, 8>);
   const size_t smem = smem_of(W);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
