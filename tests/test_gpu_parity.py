@@ -301,6 +301,24 @@ def test_gradient_modes_checkpointed():
     _grad_check(inst, tie_free=False)
 
 
+def test_gradient_repeat_calls_agree():
+    """Two gradient calls on the same solve agree to float32 rounding (the
+    occupancy scatter adds with atomics, so the order of its float sums, and
+    with it the last bits, may differ between calls; the cross-CTA sums are
+    in a fixed order)."""
+    inst = I.random_instance(55, 30, 150, 6, 10, 12, 2, neg_prob=0.2, switch_cost=3.0)
+    inst.s0 = 70
+    inst.ckpt_every = 8
+    s, _ = solve_gpu(inst)
+    mu0 = np.full(inst.K, 1.0 / inst.K, np.float32)
+    a = s.grad(0, mu0, extra=True)
+    b = s.grad(0, mu0, extra=True)
+    for x, y in zip(a, b):
+        x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
+        scale = max(np.abs(x).max(), 1e-30)
+        assert np.abs(x - y).max() <= 1e-5 * scale
+
+
 def test_gradient_config5():
     n = _grad_check(I.config5(), tie_free=False)
     print(f"config5: {n} near-tie decisions differ from the FP64 oracle's")
