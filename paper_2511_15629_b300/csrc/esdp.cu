@@ -1059,7 +1059,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   }
   // workspace: carved from the context's gradient scratch (kept across calls)
   void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
-      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs;
+      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs, *dtpart, *dtmass;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
   const int MN = M * N;
   int ogrid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));  // occupancy CTAs
@@ -1068,13 +1068,14 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   {
     void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
                      &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
-                     &opart_acc, &dsegs};
+                     &opart_acc, &dsegs, &dtpart, &dtmass};
     const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
                             (size_t)T * K * 8, 8 * 8, 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
                             (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
                             (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
-                            (size_t)nseg * sizeof(AssetDev)};
+                            (size_t)nseg * sizeof(AssetDev), (size_t)C * 4 * K * K * 8,
+                            (size_t)C * 4 * K * 8};
     size_t total = 0;
     for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
     if (total > c->grad_scr_bytes) {
@@ -1089,7 +1090,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
       c->grad_scr_bytes = total;
     }
     char* q = (char*)c->grad_scr;
-    for (int i = 0; i < 18; ++i) {
+    for (int i = 0; i < 20; ++i) {
       *outs[i] = q;
       q += (sizes[i] + 255) / 256 * 256;
     }
@@ -1195,6 +1196,8 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     dp.vnext = (const float*)seg_v + L;
     dp.cnext = c->d_off[asset] + t_lo + 1;
     dp.d_trans = (float*)dtr + (size_t)(t_lo - 1) * K * K;
+    dp.part = (double*)dtpart;
+    dp.part_mass = (double*)dtmass;
     if ((e = launch_dtrans(dp, st)) != cudaSuccess) return cfail(e, "dtrans");
   }
   const long long nP = (long long)T * K;

@@ -230,6 +230,8 @@ struct DTransParams {
   const float* vnext;   // V'_{t+1} for the n_t stages: [n_t][MN][K]
   const double* cnext;  // [n_t]: c_{t+1}, V_{t+1} = V'_{t+1} + c_{t+1}
   float* d_trans;       // [n_t][K][K]
+  double* part;         // [n_t][4][K][K] row-quarter partial sums (scratch)
+  double* part_mass;    // [n_t][4][K] row-quarter occupancy masses (scratch)
 };
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream);
 

@@ -161,20 +161,26 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
 }
 
 // dJ/dP_t = post_t^T V_{t+1} over all rows (m, s): one block per (stage,
-// 32 x 32 tile of (k, k2)).  Lane l of every warp owns column k2 = 32 tx + l
-// and keeps the 32 sums of its tile rows k = 32 ty + j in registers; the 16
-// warps take interleaved rows, two per iteration with every load issued
-// before the FMAs (a warp's post values of a row are broadcast reads of four
-// at a time).  The warp partials are added in double in a fixed order (the
-// upper eight warps' first, through shared memory), then c_{t+1} times the
-// occupancy mass of k (V_{t+1} = V'_{t+1} + c_{t+1}).  Deterministic.
+// 32 x 32 tile of (k, k2), quarter of the rows).  Lane l of every warp owns
+// column k2 = 32 tx + l and keeps the 32 sums of its tile rows k = 32 ty + j
+// in registers; the 16 warps take interleaved rows of the block's quarter,
+// two at a time with every load issued before the FMAs (a warp's post values
+// of a row are broadcast reads of four at a time).  The warp partials are
+// added in double in a fixed order (the upper eight warps' first, through
+// shared memory) into the block's partial; dtrans_finish_kernel adds the
+// quarters in order plus c_{t+1} times the occupancy mass of k
+// (V_{t+1} = V'_{t+1} + c_{t+1}).
 constexpr int kDtWarps = 16;
+constexpr int kDtSplit = 4;
 __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParams p) {
   __shared__ float s_acc[kDtWarps / 2][32][33];
   __shared__ float s_mass[kDtWarps][32];
   const int K = p.K, MN = p.MN;
   const int tiles = (K + 31) / 32;
   const int ts = blockIdx.y, ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
+  const int part = blockIdx.z;
+  const int row0 = (int)((long long)MN * part / kDtSplit);
+  const int row1 = (int)((long long)MN * (part + 1) / kDtSplit);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k2 = 32 * tx + lane, kb = 32 * ty;
   const int nk = min(32, K - kb);
@@ -185,9 +191,9 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
   float mass = 0.f;
   const bool vec = (K & 3) == 0 && nk == 32;
-  for (int row = w; row < MN; row += 2 * kDtWarps) {
+  for (int row = row0 + w; row < row1; row += 2 * kDtWarps) {
     const int rb = row + kDtWarps;
-    const bool two = rb < MN;
+    const bool two = rb < row1;
     const float* pa = post + (size_t)row * K + kb;
     const float* pb = post + (size_t)(two ? rb : row) * K + kb;
     const float va = k2 < K ? __ldg(v + (size_t)row * K + k2) : 0.f;
@@ -234,17 +240,40 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
     for (int j = 0; j < 32; ++j) s_acc[w][j][lane] = acc[j];
   }
   __syncthreads();
+  // this block's partial: [ts][part][k][k2] sums and [ts][part][k] masses
+  double* ps = p.part + ((size_t)ts * kDtSplit + part) * K * K;
+  double* pm = p.part_mass + ((size_t)ts * kDtSplit + part) * K;
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int j = e >> 5, l = e & 31;
     const int k = kb + j, kk2 = 32 * tx + l;
     if (k >= K || kk2 >= K) continue;
-    double sv = 0.0, sm = 0.0;
+    double sv = 0.0;
 #pragma unroll
     for (int q = 0; q < half; ++q) sv += (double)s_acc[q][j][l];
+    ps[(size_t)k * K + kk2] = sv;
+    if (tx == 0 && l == 0) {
+      double sm = 0.0;
 #pragma unroll
-    for (int q = 0; q < kDtWarps; ++q) sm += (double)s_mass[q][j];
-    p.d_trans[(size_t)ts * K * K + (size_t)k * K + kk2] = (float)(sv + p.cnext[ts] * sm);
+      for (int q = 0; q < kDtWarps; ++q) sm += (double)s_mass[q][j];
+      pm[k] = sm;
+    }
   }
+}
+
+// dJ/dP_t[k][k2] = sum of the row quarters in order + c_{t+1} mass_t[k]
+__global__ void dtrans_finish_kernel(const DTransParams p) {
+  const int K = p.K;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)p.n_t * K * K) return;
+  const int ts = (int)(i / ((long long)K * K));
+  const int e = (int)(i - (long long)ts * K * K), k = e / K;
+  double sv = 0.0, sm = 0.0;
+#pragma unroll
+  for (int q = 0; q < kDtSplit; ++q) {
+    sv += p.part[((size_t)ts * kDtSplit + q) * K * K + e];
+    sm += p.part_mass[((size_t)ts * kDtSplit + q) * K + k];
+  }
+  p.d_trans[(size_t)ts * K * K + e] = (float)(sv + p.cnext[ts] * sm);
 }
 
 // Per-CTA partials of one segment into the accumulated gradients, one warp
@@ -301,7 +330,11 @@ cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream) {
   if (p.n_t == 0) return cudaSuccess;
   const int tiles = (p.K + 31) / 32;
-  dtrans_kernel<<<dim3(tiles * tiles, p.n_t), 32 * kDtWarps, 0, stream>>>(p);
+  dtrans_kernel<<<dim3(tiles * tiles, p.n_t, kDtSplit), 32 * kDtWarps, 0, stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)p.n_t * p.K * p.K;
+  dtrans_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(p);
   return cudaGetLastError();
 }
 
