@@ -1257,9 +1257,10 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int> ids(c->assets.size());
   std::iota(ids.begin(), ids.end(), 0);
-  // time every candidate on zero inputs over a short horizon: the cost of
-  // the sweep does not depend on the values
-  const int t_short = 8;
+  // time every candidate on zero inputs over a short horizon (the cost of
+  // the sweep does not depend on the values): best of four launches after a
+  // warm-up, so that run-to-run noise rarely decides between close shapes
+  const int t_short = 16;
   float *zp = nullptr, *zt = nullptr, *zc = nullptr, *zm = nullptr;
   int rc;
   if ((rc = dalloc(c, &zp, c->n_price)) || (rc = dalloc(c, &zt, c->n_trans)) ||
@@ -1307,7 +1308,7 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
       for (const AssetDev& d : p.adev) p.n_steps = std::max(p.n_steps, d.t_hi - d.t_lo + 1);
       double ms = 1e300;
       if (ok) {
-        for (int rep = 0; rep < 3 && ok; ++rep) {
+        for (int rep = 0; rep < 5 && ok; ++rep) {
           cudaEventRecord(e0, st);
           if (run_plan(c, &p, zp, zt, zc, zm, nullptr, st)) {
             ok = false;
