@@ -14,8 +14,8 @@
 // a tile of SoC rows stages a single column of V_t (its rows plus the action
 // halo), forms the feasible, interpolated next values once per (row, action),
 // and every price sample of the row reuses them; a thread owns one row and
-// KG samples (8 or 10, whichever needs fewer passes of the block over the
-// tile's rows for its work) and runs the max over all actions for them.
+// KG samples (6, 8 or 10: the least work per thread for the tile's rows,
+// passes of the block x samples) and runs the max over all actions for them.
 //
 // Persistent cooperative launch over all stages; tiles synchronise with their
 // neighbours only (release/acquire flags, bounded waits) as in the main sweep.
@@ -566,7 +566,7 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     dmin = std::min(dmin, dlo[a]);
     dmax = std::max(dmax, dlo[a] + (fr > 0 ? 1 : 0));
   }
-  const int groups8 = (R + kIidKG - 1) / kIidKG;  // the larger group count (shared memory)
+  const int groups8 = (R + 5) / 6;  // the largest group count, KG = 6 (shared memory)
   int dev_id = 0, n_sm = 0;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev_id);
@@ -631,18 +631,21 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
          (!terminal || h2d(d_term, terminal, (size_t)S * 4));
   }
   // samples per thread: the block takes rows in passes of kIidBlock / groups
-  // rows; of 8 and 10 samples the one with less work per thread for a tile
-  // (passes x samples) wins, 8 on ties
+  // rows; of 6, 8 and 10 samples the one with the least work per thread for a
+  // tile (passes x samples) wins, 8 on ties
   auto work = [&](int kg) {
     const int g = (R + kg - 1) / kg, rows_pass = kIidBlock / g;
     return rows_pass < 1 ? 1 << 30 : ((W + rows_pass - 1) / rows_pass) * kg;
   };
-  const int KG = work(10) < work(8) ? 10 : 8;
+  int KG = 8;
+  if (work(10) < work(KG)) KG = 10;
+  if (work(6) < work(KG)) KG = 6;
   const int groups = (R + KG - 1) / KG;
   // launch shape: one CTA per SM at most, contiguous tile ranges
   const bool pk = policy && q->policy_bytes;
   auto fn = KG == 10 ? (pk ? iid_kernel<true, 10> : iid_kernel<false, 10>)
-                     : (pk ? iid_kernel<true, 8> : iid_kernel<false, 8>);
+            : KG == 6 ? (pk ? iid_kernel<true, 6> : iid_kernel<false, 6>)
+                      : (pk ? iid_kernel<true, 8> : iid_kernel<false, 8>);
   const size_t smem = smem_of(W);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
