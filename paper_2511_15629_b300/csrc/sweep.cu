@@ -1194,8 +1194,11 @@ int max_blocks_R(int block, size_t smem) {
 cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows,
                            const float* trans, cudaStream_t stream) {
   if (n_assets == 0) return cudaSuccess;
+  // enough threads for the prepared copy (about 32 elements per row), not
+  // only for the row sums: its loads are then in flight together
   const int block = 128;
-  const int gx = std::max(1, std::min(256, (max_rows + block - 1) / block));
+  const long long elems = (long long)max_rows * 32;
+  const int gx = (int)std::max(1LL, std::min(2048LL, (elems + block - 1) / block));
   rowsum_kernel<<<dim3(gx, n_assets), block, 0, stream>>>(d_assets, trans);
   return cudaGetLastError();
 }
