@@ -252,14 +252,24 @@ __global__ void __launch_bounds__(kIidBlock, 1) iid_kernel(const IidParams p) {
             }
           }
         } else {
+          // the same candidates two samples per packed FMA; the argmax with a
+          // strict > over ascending actions (the smallest maximiser)
+          unsigned long long lam2[KG / 2];
+#pragma unroll
+          for (int j = 0; j < KG / 2; ++j) lam2[j] = pack2(lam[2 * j], lam[2 * j + 1]);
           for (int a = 0; a < P; ++a) {
             const float2 bp = Br[a];
+            const unsigned long long b2 = pack2(bp.x, bp.x), p2 = pack2(bp.y, bp.y);
 #pragma unroll
-            for (int j = 0; j < KG; ++j) {
-              const float v = fmaf(lam[j], bp.y, bp.x);
-              if (v > best[j]) {
-                best[j] = v;
-                arg[j] = a;
+            for (int j = 0; j < KG / 2; ++j) {
+              const float2 c = fma2u(lam2[j], p2, b2);
+              if (c.x > best[2 * j]) {
+                best[2 * j] = c.x;
+                arg[2 * j] = a;
+              }
+              if (c.y > best[2 * j + 1]) {
+                best[2 * j + 1] = c.y;
+                arg[2 * j + 1] = a;
               }
             }
           }
