@@ -1070,7 +1070,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
                      &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
                      &opart_acc, &dsegs, &dtpart, &dtmass};
     const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
-                            (size_t)T * K * 8, 8 * 8, 4, (size_t)K * 4, 8,
+                            (size_t)T * K * 8, 8 * 8, (size_t)ogrid * 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
                             (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
                             (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
@@ -1159,7 +1159,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
                              st)) != cudaSuccess)
       return cfail(e, "segment copy");
     cudaMemsetAsync(seg_post, 0, L * nt * 4, st);
-    cudaMemsetAsync(bar, 0, 4, st);
+    cudaMemsetAsync(bar, 0, (size_t)ogrid * 4, st);
     OccParams op{};
     op.N = N; op.K = K; op.M = M; op.A = a.A; op.D_dis = a.D_dis;
     op.t_lo = t_lo; op.t_hi = t_hi;
@@ -1183,7 +1183,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.part = (double*)opart;
     op.part_cost = (double*)opart_cost;
     op.part_acc = (double*)opart_acc;
-    op.bar = (int*)bar;
+    op.flags = (int*)bar;
     op.status = c->d_status;
     op.timeout_ns = c->timeout_ns;
     if ((e = launch_occupancy(op, grid, 256, st)) != cudaSuccess) return cfail(e, "occupancy");

@@ -215,7 +215,7 @@ struct OccParams {
   double* part;           // [C][grid][K] per-CTA stage partials of dprice
   double* part_cost;      // [grid][A] per-CTA segment partials of d_cost
   double* part_acc;       // [grid][8] per-CTA segment partials of acc
-  int* bar;               // grid barrier counter (zero on entry)
+  int* flags;             // [grid] last stage whose scatter each CTA published (zero on entry)
   int* status;
   unsigned long long timeout_ns;
 };

@@ -16,8 +16,9 @@
 //   dJ/dswitch             = -sum rho_t [m = 1, d < 0]                  (two modes)
 //   dJ/dterminal           = rho_{T+1}, dJ/dmu0[k] = V_1[0][s0][k]  (taken by the host)
 // occ_kernel runs the forward pass over a segment of stages in one
-// cooperative launch (one bounded grid barrier per stage, between the scatter
-// and the contraction); dtrans_kernel then forms dJ/dP for the segment from
+// cooperative launch (per stage, between the scatter and the contraction, a
+// CTA waits only for the CTAs whose rows can scatter into its own: release
+// flags and bounded acquire polls); dtrans_kernel then forms dJ/dP for the segment from
 // the stored post-decision occupancies and values (a split-row reduction per
 // stage and 32 x 32 output tile).
 #include <cuda_runtime.h>
@@ -40,25 +41,63 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-__device__ bool grid_barrier(int* bar, int target, int* status, unsigned long long timeout,
-                             int* s_abort) {
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// This CTA's scatter of stage `epoch` is complete: its atomics on the
+// post-decision occupancy are ordered before the flag (barrier, fence,
+// release store by one thread).
+__device__ __forceinline__ void publish_stage(int* flags, int epoch) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(bar, 1);
-    const unsigned long long t0 = now_ns();
-    while (ld_acquire(bar) < target) {
-      if (*(volatile int*)status != 0) {
-        *(volatile int*)s_abort = 1;
+    st_release(flags + blockIdx.x, epoch);
+  }
+}
+
+// Wait until every CTA that can scatter into this CTA's rows [r0, r1) has
+// published stage `epoch`.  A target (m', s') receives from (m, s) with
+// s' - D_chg <= s <= s' + D_dis in every mode m, so the sources are the CTAs
+// covering rows m N + [lo, hi] of each mode.  Each thread polls a share of
+// them with acquire loads, bounded by the timeout (status ESDP_ETIMEOUT).
+__device__ bool wait_sources(const OccParams& p, int r0, int r1, int epoch, int* s_abort) {
+  const int N = p.N, gr = p.grid_rows, D_chg = p.A - 1 - p.D_dis;
+  const int m0 = r0 / N, m1 = (r1 - 1) / N;
+  int s_lo = 0, s_hi = N - 1;  // the rows' SoC range (all of it across a mode boundary)
+  if (m0 == m1) {
+    s_lo = r0 - m0 * N;
+    s_hi = r1 - 1 - m0 * N;
+  }
+  const int lo = max(0, s_lo - D_chg), hi = min(N - 1, s_hi + p.D_dis);
+  // CTA range [c0_m, c1_m] of each mode's rows m N + [lo, hi]
+  int total = 0;
+  for (int m = 0; m < p.M; ++m) total += (m * N + hi) / gr - (m * N + lo) / gr + 1;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    int rem = q, cta = 0;
+    for (int m = 0; m < p.M; ++m) {
+      const int c0 = (m * N + lo) / gr, c1 = (m * N + hi) / gr;
+      if (rem <= c1 - c0) {
+        cta = c0 + rem;
         break;
       }
-      if (now_ns() - t0 > timeout) {
-        atomicCAS(status, 0, ESDP_ETIMEOUT);
-        *(volatile int*)s_abort = 1;
-        break;
+      rem -= c1 - c0 + 1;
+    }
+    const unsigned long long t0 = now_ns();
+    int polls = 0;
+    while (ld_acquire(p.flags + cta) < epoch) {
+      if ((++polls & 15) == 0) {
+        if (*(volatile int*)p.status != 0) {
+          *(volatile int*)s_abort = 1;
+          break;
+        }
+        if (now_ns() - t0 > p.timeout_ns) {
+          atomicCAS(p.status, 0, ESDP_ETIMEOUT);
+          *(volatile int*)s_abort = 1;
+          break;
+        }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int*)s_abort == 0;
@@ -147,7 +186,8 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       if (tid < 8) p.part_acc[(size_t)blockIdx.x * 8 + tid] = sacc[tid];
     }
     ++epoch;
-    if (!grid_barrier(p.bar, epoch * (int)gridDim.x, p.status, p.timeout_ns, &s_abort)) return;
+    publish_stage(p.flags, epoch);
+    if (!wait_sources(p, r0, r1, epoch, &s_abort)) return;
     // contraction of the post-decision occupancy with P_t (own rows)
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const int row = i / K, k2 = i - row * K;
