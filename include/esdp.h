@@ -182,7 +182,10 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
               float* d_mu0, void* stream);
 
 /* Re-time the candidate tile shapes / actions-per-warp on the device and
- * keep the fastest (results are cached per shape class for the process). */
+ * keep the fastest (results are cached per shape class for the process).
+ * With the environment variable ESDP_SHAPE="R,block" (rows per thread
+ * 4/6/8/10/12, threads per block) that shape is used without timing;
+ * ESDP_EINVAL if it cannot be built for the context's assets. */
 int esdp_autotune(esdp_ctx* ctx, void* stream);
 
 /* Device status word of the last launch: 0, or the ESDP_E* code a kernel

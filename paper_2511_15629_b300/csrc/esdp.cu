@@ -1257,6 +1257,26 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int> ids(c->assets.size());
   std::iota(ids.begin(), ids.end(), 0);
+  // ESDP_SHAPE="R,block" pins the launch shape instead of timing candidates
+  // (reproducible launches, e.g. for profiler captures)
+  if (const char* f = getenv("ESDP_SHAPE")) {
+    int R = 0, block = 0;
+    if (sscanf(f, "%d,%d", &R, &block) != 2)
+      return fail(c, ESDP_EINVAL, "ESDP_SHAPE must be \"R,block\"");
+    Plan p;
+    int rc = build_plan(c, ids, R, block, c->n_sm, &p);
+    if (rc) return rc;
+    free_plan(&p);
+    g_tune_cache[TuneKey{signature(c, ids)}] = {R, block};
+    free_plan(&c->main);
+    if ((rc = build_plan(c, ids, R, block, c->n_sm, &c->main))) return rc;
+    bind_main(c, &c->main);
+    for (Plan& sp : c->solo) {
+      free_plan(&sp);
+      sp = Plan();
+    }
+    return ESDP_OK;
+  }
   // time every candidate on zero inputs over a short horizon (the cost of
   // the sweep does not depend on the values): best of four launches after a
   // warm-up, so that run-to-run noise rarely decides between close shapes

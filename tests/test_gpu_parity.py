@@ -504,6 +504,24 @@ def test_bid_curves_envelope_shapes(N, shape):
     _hull_gpu_vs_oracle(inst)
 
 
+def test_autotune_shape_pin(monkeypatch):
+    """ESDP_SHAPE pins the launch shape (no timing); a malformed value is
+    rejected; results do not depend on the shape."""
+    inst = I.random_instance(77, 9, 333, 7, 13, 17, 1)
+    ref = solve_gpu(inst)[1]
+    monkeypatch.setenv("ESDP_SHAPE", "6,384")
+    s = E.Solver([inst])
+    s.autotune()
+    info = s.launch_info()
+    assert info["rows_per_thread"] == 6 and info["block"] == 384
+    V1 = s.solve_instances()[0]
+    np.testing.assert_allclose(V1, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    monkeypatch.setenv("ESDP_SHAPE", "six")
+    with pytest.raises(E.EsdpError) as ei:
+        E.Solver([inst]).autotune()
+    assert ei.value.code == E.ESDP_EINVAL
+
+
 # ------------------------------------------------- packed bid curves
 
 def test_bid_curves_packed_equal_padded():
