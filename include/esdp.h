@@ -146,7 +146,8 @@ int esdp_bid_curves_packed(esdp_ctx* ctx, int32_t asset, int32_t t0, int32_t t1,
  * would exceed its selling price g / eta_d (g < 0) the envelope merges the
  * two sides.  Inputs n_bp [n][M][K], bp_idx [n][M][K][N] as esdp_bid_curves
  * wrote them (n = t1 - t0); outputs n_pts [n][M][K] (breakpoint count,
- * >= 1), p_mw [n][M][K][A] (double), price [n][M][K][A] (float, the first
+ * >= 1; 0 where the input was not a vertex list of 2..N strictly increasing
+ * indices from 0 to N-1), p_mw [n][M][K][A] (double), price [n][M][K][A] (float, the first
  * n_pts - 1 used).  Needs ESDP_KEEP_EV and a completed solve.  Device or
  * host pointers as the context's flags say; host mode blocks.  Returns
  * ESDP_EINVAL (NULL pointer, bad asset, stage range or s), ESDP_ESTATE,

@@ -63,6 +63,14 @@ __global__ void __launch_bounds__(128) bids_at_kernel(const BidsAtParams p) {
   double* pw = p.p_mw + (size_t)h * p.A;
   float* pr = p.price + (size_t)h * p.A;
   int* xs = reinterpret_cast<int*>(pr);  // the chain's SoC indices until the prices
+  // the vertex list must be an envelope's: 2..N strictly increasing indices
+  // from 0 to N-1 (else no bid, n_pts = 0, and nothing outside the row is read)
+  bool ok = nv >= 2 && nv <= N && v[0] == 0 && v[nv - 1] == N - 1;
+  for (int j = 1; ok && j < nv; ++j) ok = v[j] > v[j - 1];
+  if (!ok) {
+    p.n_pts[h] = 0;
+    return;
+  }
 
   const int s = p.s, lo = max(0, s - p.D_dis), hi = min(N - 1, s + p.D_chg);
   // vertices strictly inside (lo, hi): v[jlo .. jhi]

@@ -636,6 +636,25 @@ def test_bids_at_edge_windows(N, Dd, Dc, modes):
                         assert np.all(p_mw[t, m, k, :n] >= 0)   # nothing to buy
 
 
+def test_bids_at_rejects_invalid_vertex_lists():
+    """Vertex lists that are not an envelope's (count out of range, unsorted,
+    not spanning 0..N-1) give no bid (n_pts = 0) instead of reading outside
+    the EV row; valid ones are unaffected."""
+    inst = I.random_instance(26, 3, 80, 3, 5, 5, 1)
+    s, _ = solve_gpu(inst, keep_ev=True)
+    n_bp, idx, _ = s.bid_curves(0, 1, inst.T + 1)
+    good = s.bids_at(0, 1, inst.T + 1, 40, n_bp, idx)[0]
+    bad_n, bad_i = n_bp.copy(), idx.copy()
+    bad_n[0, 0, 0] = inst.N + 5                     # count beyond the row
+    bad_n[0, 0, 1] = 1                              # too few
+    bad_i[1, 0, 0, :2] = [5, 3]                     # not starting at 0, unsorted
+    bad_i[1, 0, 1, bad_n[1, 0, 1] - 1] = inst.N + 7  # last index outside the grid
+    n_pts = s.bids_at(0, 1, inst.T + 1, 40, bad_n, bad_i)[0]
+    assert n_pts[0, 0, 0] == 0 and n_pts[0, 0, 1] == 0
+    assert n_pts[1, 0, 0] == 0 and n_pts[1, 0, 1] == 0
+    np.testing.assert_array_equal(n_pts[2:], good[2:])
+
+
 def test_bids_at_device_pointers_equal_host():
     import torch
     inst = I.random_instance(23, 5, 200, 4, 15, 15, 2, neg_prob=0.3)
