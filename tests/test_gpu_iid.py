@@ -105,10 +105,14 @@ def test_iid_equals_markov_sweep_on_recombining_grid():
     assert np.abs(V0 - Vm).max() / scale <= 2e-5
 
 
-def test_iid_tiles_taller_than_one_pass():
-    """S = 10001 on 148 SMs gives 68-row tiles while 64 samples per row fill
-    only 64 rows per pass of the block: rows are taken in two passes."""
-    prob = I.iid_problem(10, 6, 10001, 64, 1000.0)
+@pytest.mark.parametrize("S", [10001, 7400])
+def test_iid_tiles_taller_than_one_pass(S):
+    """Tall tiles with 64 samples per row: S = 10001 gives 68-row tiles
+    (10 samples per thread take them in one pass of the block, 8 would need
+    two), S = 7400 gives 50-row tiles (8 samples per thread, one pass; 6
+    would need two).  The samples-per-thread variants are chosen by work per
+    thread, so these shapes exercise the ones the small tests do not."""
+    prob = I.iid_problem(10, 6, S, 64, 1000.0)
     _check_values(E.solve_iid(prob), _oracle(prob)[0])
 
 
