@@ -522,6 +522,25 @@ def test_autotune_shape_pin(monkeypatch):
     assert ei.value.code == E.ESDP_EINVAL
 
 
+@pytest.mark.parametrize("R,block,K", [(4, 256, 20), (6, 512, 20), (8, 256, 16), (10, 384, 20),
+                                       (12, 256, 12)])
+def test_every_rows_per_thread_variant(monkeypatch, R, block, K):
+    """Each compiled rows-per-thread variant of the sweep (pinned through
+    ESDP_SHAPE) matches the oracle's values and policies; K = 16 takes the
+    tensor-core EV path, the others SIMT."""
+    inst = I.random_instance(90 + R, 6, 301, K, 30, 24, 2, neg_prob=0.2, cost="nonconvex")
+    monkeypatch.setenv("ESDP_SHAPE", f"{R},{block}")
+    s = E.Solver([inst])
+    s.autotune()
+    info = s.launch_info()
+    assert info["rows_per_thread"] == R and info["block"] == block
+    V1 = s.solve_instances()[0]
+    r = O.solve(inst, nthreads=NTHREADS)
+    scale = _scale(r["V1"])
+    assert_values(V1, r["V1"], scale)
+    assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale)
+
+
 # ------------------------------------------------- packed bid curves
 
 def test_bid_curves_packed_equal_padded():
