@@ -91,6 +91,9 @@ RANDOM_CASES = [
     (5, 64, 7, 9, 0, 2, 8, "linear"),       # discharge-only band with modes
     (12, 777, 16, 33, 31, 2, 9, "nonconvex"),
     (2, 5001, 5, 100, 100, 1, 10, "linear"),
+    (3, 200, 128, 10, 10, 2, 11, "nonconvex"),  # largest K: tensor-core EV, two modes
+    (3, 150, 127, 7, 9, 1, 12, "linear"),       # largest odd K (SIMT EV)
+    (3, 2000, 4, 600, 700, 1, 13, "linear"),    # A = 1301: a very wide band
 ]
 
 
