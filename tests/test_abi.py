@@ -131,7 +131,8 @@ def test_iid_action_grid_matches_tables_and_oracle(lib):
 def test_iid_rejects_bad_problems(lib):
     from paper_2511_15629_b300 import instances as I
     prob = I.iid_problem(1, 3, 11, 4, 1.0)
-    for field, value in [("eta", 1.5), ("S", 1), ("R", 0), ("policy_bytes", 3), ("tau", 0.0)]:
+    for field, value in [("eta", 1.5), ("S", 1), ("R", 0), ("R", 4097), ("policy_bytes", 3),
+                         ("tau", 0.0)]:
         bad = dataclasses.replace(prob, **{field: value})
         with pytest.raises(E.EsdpError) as ei:
             E.solve_iid(bad, policy_bytes=getattr(bad, "policy_bytes"))

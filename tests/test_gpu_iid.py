@@ -241,6 +241,7 @@ def test_iid_clearing_monte_carlo_reproduces_value():
     dict(S=11, R=3, hours=1.0, p_max=0.03),            # p_max below one SoC step: P = 3
     dict(S=21, R=4, hours=0.5, p_max=2.0),             # end points beyond the whole range
     dict(S=301, R=9, hours=30.0, p_max=5.0),           # wide action grid, halo over many tiles
+    dict(S=21, R=4096, hours=2.0),                     # the most samples per stage
 ])
 def test_iid_edge_shapes(kw):
     hours = kw.pop("hours")
