@@ -96,6 +96,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
                : "memory");
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -185,6 +190,7 @@ struct Smem {
   float2* EC;      // [M][rs] (grid energy e_a, -(cost_a + switch)), -inf padding
   double* lvl;     // [2]: c_{t+1}, c_t
   float* lam;      // [K] prices of the stage
+  double* rho;     // [K] row sums of P_{t-1}
   float* delta;    // [K] level correction of the stage
   float* ref;      // EV'_t[ref]
   int* abort;
@@ -634,23 +640,24 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
   }
 }
 
-// Per-thread scalars of stage t of work item `it`: threads below K hold the
-// price and the row sum of P_{t-1} of their state, thread 0 the item's running
-// level c_{t+1}.
+// Inputs of stage t of work item `it` that do not depend on other tiles:
+// threads below K start copies of the price and the row sum of P_{t-1} of
+// their state into shared memory (waited for in the stage with
+// cp.async.wait_all), thread 0 takes the item's running level c_{t+1} (from
+// shared memory when the item repeats, else from its global slot).
 struct StageScalars {
-  float lam = 0.f;
-  double rho = 0.0, c = 0.0;
+  double c = 0.0;
   bool valid = false;
 };
 
 __device__ __forceinline__ void stage_scalars(const SweepParams& p, const AssetDev& as, int t,
-                                              int it, float& lam, double& rho, double& c) {
+                                              int it, const Smem& sm, double& c, bool same) {
   const int K = as.K, tid = threadIdx.x;
   if (tid < K) {
-    lam = __ldg(p.price + as.off_price + (size_t)(t - 1) * K + tid);
-    rho = __ldg(as.rho + (size_t)(t - 1) * K + tid);
+    cp_async4(sm.lam + tid, p.price + as.off_price + (size_t)(t - 1) * K + tid);
+    cp_async8(sm.rho + tid, as.rho + (size_t)(t - 1) * K + tid);
   }
-  if (tid == 0) c = *(volatile double*)(p.item_c + it);
+  if (tid == 0) c = same ? sm.lvl[1] : *(volatile double*)(p.item_c + it);
 }
 
 __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const WorkItem& w, int t,
@@ -679,9 +686,8 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   // scalars (price, row sum, running level) may already be in flight, issued
   // right after the previous stage's release
   const bool p_bulk = p_pref || (t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP));
-  float lam_k = pre.lam;
-  double rho_k = pre.rho, c_next = pre.c;
-  if (!pre.valid) stage_scalars(p, as, t, it, lam_k, rho_k, c_next);
+  double c_next = pre.c;
+  if (!pre.valid) stage_scalars(p, as, t, it, sm, c_next, false);
 
   // 1. neighbours; meanwhile the warps that do not poll write the previous
   //    stage's outputs (its V' tile and indices are still in place)
@@ -737,15 +743,14 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     p.item_c[it] = c_t;
     if (w.tile == 0) as.off[t] = c_t;
   }
+  cp_async_wait_all();
   __syncthreads();
   if (tid < K) {
-    const double cr = sm.lvl[0] * rho_k;
+    const double cr = sm.lvl[0] * sm.rho[tid];
     sm.delta[tid] = (float)(cr - sm.lvl[1]);
-    sm.lam[tid] = lam_k;
     if (w.tile == 0) as.evoff[(size_t)(t - 1) * K + tid] = cr;
   }
   if (tid == K && (K & 1)) sm.lam[K] = 0.f;  // pad state of an odd K
-  cp_async_wait_all();
   if (tma) {
     if (tid == 0 && !mbar_wait_bounded(sm.bar, parity, p)) *(volatile int*)sm.abort = 1;
     parity ^= 1u;
@@ -1053,7 +1058,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         pref = next && as.ptrans != nullptr && nt > as.t_lo;
         if (pref) load_trans_async(p, as, nt - 1, sm.Ps, sm.barP);
         pre.valid = next;
-        if (next) stage_scalars(p, as, nt, nit, pre.lam, pre.rho, pre.c);
+        if (next) stage_scalars(p, as, nt, nit, sm, pre.c, nit == it);
         // this stage's outputs: during the next stage's wait when one follows
         // on this asset, else now
         if (next) {
@@ -1077,6 +1082,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   __shared__ double s_lvl[2];
   __shared__ float s_lam[128];
   __shared__ float s_delta[128];
+  __shared__ double s_rho[128];
   __shared__ float s_ref;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ __align__(8) uint64_t s_barP;
@@ -1094,6 +1100,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   sm.lvl = s_lvl;
   sm.lam = s_lam;
   sm.delta = s_delta;
+  sm.rho = s_rho;
   sm.ref = &s_ref;
   sm.abort = &s_abort;
   sm.bar = &s_bar;
