@@ -186,7 +186,10 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
  * keep the fastest (results are cached per shape class for the process).
  * With the environment variable ESDP_SHAPE="R,block" (rows per thread
  * 4/6/8/10/12, threads per block) that shape is used without timing;
- * ESDP_EINVAL if it cannot be built for the context's assets. */
+ * ESDP_EINVAL if it cannot be built for the context's assets.  The results
+ * of an earlier esdp_solve are discarded (the timed launches reuse the
+ * context's workspace): policy, EV, bid curves and esdp_grad answer
+ * ESDP_ESTATE until the next solve. */
 int esdp_autotune(esdp_ctx* ctx, void* stream);
 
 /* Device status word of the last launch: 0, or the ESDP_E* code a kernel
@@ -194,9 +197,15 @@ int esdp_autotune(esdp_ctx* ctx, void* stream);
 int esdp_status(esdp_ctx* ctx, void* stream);
 
 /* Counters of the chosen launch shape: grid, block, work items, rows per
- * tile of asset 0, actions split (parts), R (rows per thread).  Any may be NULL. */
+ * tile of asset 0, actions split (parts), R (rows per thread), and the unit
+ * that contracts EV for asset 0 (ev_path: 0 FP32 SIMT, 1 tcgen05 split-tf32,
+ * 2 mma.sync split-tf32; tiles of at least 98,304 multiply-adds per stage,
+ * rows x modes x K^2, take a tensor path when K is a multiple of 16 resp. 8;
+ * the environment variable ESDP_EV = "simt" | "tc" | "mma" pins one where K
+ * allows it).  Any pointer may be NULL. */
 int esdp_launch_info(const esdp_ctx* ctx, int32_t* grid, int32_t* block, int32_t* items,
-                     int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread);
+                     int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread,
+                     int32_t* ev_path);
 
 /* ---------------------------------------------------------------------
  * Stagewise-independent prices on the paper's own action grid (Sec. III-A,

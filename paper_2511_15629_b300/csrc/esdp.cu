@@ -99,6 +99,7 @@ struct esdp_ctx {
   const float* last_terminal = nullptr;
   const float* last_v1 = nullptr;
   bool solved = false;
+  std::vector<int> prep_tc;       // per asset: tc flag of its last P preparation (-1: none)
   Plan main;
   std::vector<Plan> solo;         // per-asset plans for the gradient recompute
   std::string err;
@@ -179,8 +180,22 @@ struct AssetChoice {
   int nb, parts, W, n_tiles, rows, rs;
 };
 
+// ESDP_EV = "simt" | "tc" | "mma" pins the EV contraction path where K
+// allows it (so that every path can be exercised on small grids); otherwise
+// the path follows the tile's contraction size (ev_path).
+int ev_force() {
+  const char* f = getenv("ESDP_EV");
+  if (!f) return 0;
+  if (!strcmp(f, "simt")) return 1;
+  if (!strcmp(f, "tc")) return 2;
+  if (!strcmp(f, "mma")) return 3;
+  return 0;
+}
+
+int asset_ev_path(const esdp_asset& a, int W) { return ev_path(W, a.n_modes, a.K, ev_force()); }
+
 size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R) {
-  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R, tc_shape(a.K)).bytes;
+  return sweep_smem_layout(a.n_modes, a.K, ch.W, a.A, R, asset_ev_path(a, ch.W) == kEvTc).bytes;
 }
 
 int n_chunks_min(const esdp_asset& a, int R) {
@@ -254,7 +269,7 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
                   "asset %d (K=%d, modes=%d, A=%d) does not fit a %d-thread tile in shared memory",
                   ids[j], a.K, a.n_modes, a.A, block);
     {
-      const bool tc = tc_shape(a.K);
+      const bool tc = asset_ev_path(a, ch[j].W) == kEvTc;
       const SweepSmem L = sweep_smem_layout(a.n_modes, a.K, ch[j].W, a.A, R, tc);
       const long long endX = L.X + ((long long)a.n_modes * ch[j].W * a.K + 31) / 32 * 32;
       need_A = std::max<long long>(need_A, L.A2 - L.A);
@@ -299,7 +314,12 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     d.evoff = c->d_evoff[ids[j]];
     d.c_start = nullptr;
     d.ptrans = c->d_ptrans[ids[j]];
-    d.tc = (d.ptrans != nullptr && tc_shape(a.K)) ? 1 : 0;  // the prepared layout follows K
+    {
+      // the prep kernel lays P out for the path of the plan that runs it
+      const int path = asset_ev_path(a, d.W);
+      d.tc = (d.ptrans != nullptr && path == kEvTc) ? 1 : 0;
+      d.mma = path == kEvMma ? 1 : 0;
+    }
     plan->max_rows = std::max(plan->max_rows, a.T * a.K);
     plan->adev.push_back(d);
     for (int tI = 0; tI < d.n_tiles; ++tI) {
@@ -440,8 +460,10 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
   sp.tmem_cols = p->tmem_cols;
   CK(cudaMemsetAsync(p->d_flags, 0, std::max(1, p->n_flags) * sizeof(int), st), "reset flags");
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "reset status");
-  if (prep)
+  if (prep) {
     CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
+    for (size_t j = 0; j < p->adev.size(); ++j) c->prep_tc[p->asset_ids[j]] = p->adev[j].tc;
+  }
   CK(launch_sweep(p->shape, sp, st), "sweep launch");
   return ESDP_OK;
 }
@@ -655,7 +677,9 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
     c->d_evoff.push_back(evoff);
     c->d_refh.push_back(refh);
     float* pt = nullptr;
-    const size_t per = tc_shape(a.K) ? 2 * (size_t)a.K * a.K : (size_t)a.K * p_stride(a.K);
+    // room for either layout: the tile size of the plan picks the EV path
+    const size_t per = std::max(tc_shape(a.K) ? 2 * (size_t)a.K * a.K : (size_t)0,
+                                (size_t)a.K * p_stride(a.K));
     if ((rc = dalloc(c, &pt, (size_t)a.T * per))) return rc;
     c->d_ptrans.push_back(pt);
   }
@@ -676,6 +700,7 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
   if ((rc = plan_default(c, ids, &c->main))) return rc;
   bind_main(c, &c->main);
   c->solo.resize(c->assets.size());
+  c->prep_tc.assign(c->assets.size(), -1);
   return ESDP_OK;
 }
 
@@ -756,8 +781,13 @@ int esdp_status(esdp_ctx* c, void* stream) {
 }
 
 int esdp_launch_info(const esdp_ctx* c, int32_t* grid, int32_t* block, int32_t* items,
-                     int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread) {
+                     int32_t* rows_per_tile, int32_t* parts, int32_t* rows_per_thread,
+                     int32_t* ev_path) {
   if (!c) return ESDP_EINVAL;
+  if (ev_path) {
+    const AssetDev* d = c->main.adev.empty() ? nullptr : &c->main.adev[0];
+    *ev_path = !d ? -1 : d->tc ? kEvTc : d->mma ? kEvMma : kEvSimt;
+  }
   if (grid) *grid = c->main.shape.grid;
   if (block) *block = c->main.shape.block;
   if (items) *items = (int32_t)c->main.items.size();
@@ -1147,9 +1177,11 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     const int t_lo = 1 + j * C, t_hi = std::min(T, (j + 1) * C);
     const int nt = t_hi - t_lo + 1;
     sp.n_steps = nt;
-    // the last solve prepared the row sums and P of these transition matrices
+    // the last solve prepared the row sums and P of these transition matrices;
+    // P again only if this plan's tile size picks another EV path (layout)
+    const bool prep = j == 0 && c->prep_tc[asset] != sp.adev[0].tc;
     if ((rc = run_plan(c, &sp, c->last_price, c->last_trans, c->last_cost, c->last_terminal,
-                       nullptr, st, false, (const AssetDev*)dsegs + j))) {
+                       nullptr, st, prep, (const AssetDev*)dsegs + j))) {
       release();
       return rc;
     }
@@ -1255,6 +1287,10 @@ extern "C" int esdp_objective(esdp_ctx* c, int32_t asset, const float* mu0, doub
 extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   if (!c) return ESDP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  // the timed candidates overwrite the context's row sums, prepared P and
+  // level offsets, and a new shape can change the P layout: the results of an
+  // earlier solve are no longer usable
+  c->solved = false;
   std::vector<int> ids(c->assets.size());
   std::iota(ids.begin(), ids.end(), 0);
   // ESDP_SHAPE="R,block" pins the launch shape instead of timing candidates

@@ -514,7 +514,7 @@ __device__ __forceinline__ void expectation(const SweepParams& p, const AssetDev
   const float* Ps = sm.Ps;
   const float* Vs = sm.Vs;
   float* dst = ev_ptr(as, te);
-  if ((as.K & 7) == 0) {
+  if (as.mma) {
     expectation_mma(as, w, te, Ps, Vs, dst);
     return;
   }

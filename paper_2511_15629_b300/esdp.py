@@ -81,7 +81,7 @@ def load_library():
     lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
     lib.esdp_status.argtypes = [vp, vp]
-    lib.esdp_launch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 6
+    lib.esdp_launch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 7
     lib.esdp_destroy.argtypes = [vp]
     lib.esdp_destroy.restype = None
     lib.esdp_last_error.argtypes = [vp]
@@ -348,11 +348,15 @@ class Solver:
     def status(self, stream=None) -> int:
         return int(self._lib.esdp_status(self._ctx, _stream(stream)))
 
+    EV_PATHS = {0: "simt", 1: "tcgen05", 2: "mma.sync"}
+
     def launch_info(self) -> dict:
-        vals = [ctypes.c_int32() for _ in range(6)]
+        vals = [ctypes.c_int32() for _ in range(7)]
         self._check(self._lib.esdp_launch_info(self._ctx, *[ctypes.byref(v) for v in vals]))
         keys = ["grid", "block", "items", "rows_per_tile", "parts", "rows_per_thread"]
-        return {k: v.value for k, v in zip(keys, vals)}
+        info = {k: v.value for k, v in zip(keys, vals)}
+        info["ev"] = self.EV_PATHS.get(vals[6].value, "none")
+        return info
 
 
 class IidProblemC(ctypes.Structure):

@@ -530,18 +530,110 @@ def test_autotune_shape_pin(monkeypatch):
 def test_every_rows_per_thread_variant(monkeypatch, R, block, K):
     """Each compiled rows-per-thread variant of the sweep (pinned through
     ESDP_SHAPE) matches the oracle's values and policies; K = 16 takes the
-    tensor-core EV path, the others SIMT."""
+    tcgen05 EV path (pinned through ESDP_EV), the others SIMT."""
     inst = I.random_instance(90 + R, 6, 301, K, 30, 24, 2, neg_prob=0.2, cost="nonconvex")
     monkeypatch.setenv("ESDP_SHAPE", f"{R},{block}")
+    monkeypatch.setenv("ESDP_EV", "tc")
     s = E.Solver([inst])
     s.autotune()
     info = s.launch_info()
     assert info["rows_per_thread"] == R and info["block"] == block
+    assert info["ev"] == ("tcgen05" if K % 16 == 0 else "simt")
     V1 = s.solve_instances()[0]
     r = O.solve(inst, nthreads=NTHREADS)
     scale = _scale(r["V1"])
     assert_values(V1, r["V1"], scale)
     assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale)
+
+
+# ------------------------------------------------- EV contraction paths
+
+EV_CASES = [
+    # path pinned, K, modes
+    ("tc", 16, 2), ("tc", 32, 1), ("tc", 64, 1), ("tc", 128, 2),
+    ("mma", 8, 2), ("mma", 24, 1), ("mma", 40, 2), ("mma", 16, 1),
+    ("simt", 16, 1), ("simt", 64, 2),
+]
+EV_NAMES = {"tc": "tcgen05", "mma": "mma.sync", "simt": "simt"}
+
+
+@pytest.mark.parametrize("path,K,M", EV_CASES, ids=[f"{p}-K{k}-M{m}" for p, k, m in EV_CASES])
+def test_ev_path_parity(monkeypatch, path, K, M):
+    """Each unit that can contract EV (pinned through ESDP_EV on grids too
+    small to pick it by themselves) gives the oracle's values, EV and
+    policies."""
+    monkeypatch.setenv("ESDP_EV", path)
+    inst = I.random_instance(500 + K + M, 5, 301, K, 20, 24, M, neg_prob=0.2, cost="nonconvex")
+    s = E.Solver([inst], keep_ev=True)
+    assert s.launch_info()["ev"] == EV_NAMES[path]
+    V1 = s.solve_instances()[0]
+    r = O.solve(inst, keep_EV=True, nthreads=NTHREADS)
+    scale = _scale(r["V1"])
+    assert_values(V1, r["V1"], scale)
+    assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale)
+    ev = np.stack([s.expected_value(0, t) for t in range(1, inst.T + 1)])
+    assert_values(ev, r["EV"], scale, "EV")
+
+
+@pytest.mark.parametrize("N,K,M", [(5001, 64, 1), (2001, 32, 1), (5001, 56, 2), (2001, 24, 2),
+                                   (1001, 128, 1), (301, 16, 2)])
+def test_ev_path_follows_tile_work(N, K, M):
+    """Without a pin the EV unit follows the contraction work of a tile,
+    rows x modes x K^2: from 98,304 multiply-adds tcgen05 (K a multiple of
+    16) or mma.sync (K a multiple of 8), below it FP32 SIMT."""
+    inst = I.random_instance(600 + K, 3, N, K, 100, 100, M)
+    s = E.Solver([inst])
+    info = s.launch_info()
+    work = info["rows_per_tile"] * M * K * K
+    want = "simt"
+    if work >= 98304:
+        want = "tcgen05" if K % 16 == 0 else ("mma.sync" if K % 8 == 0 else "simt")
+    assert info["ev"] == want
+    s.close()
+
+
+def test_autotune_discards_solve():
+    """Tuning reuses the context's workspace: after it the results of the
+    earlier solve are refused (ESDP_ESTATE) until the next solve, which
+    gives the same objective."""
+    inst = I.random_instance(61, 8, 200, 6, 12, 12, 1, neg_prob=0.2)
+    inst.s0 = 90
+    s = E.Solver([inst], keep_ev=True)
+    s.solve_instances()
+    J0 = s.grad(0, inst.mu0)[0][0]
+    s.autotune()
+    for call in (lambda: s.grad(0, inst.mu0), lambda: s.bid_curves(0, 1, 2),
+                 lambda: s.policy(0, 1)):
+        with pytest.raises(E.EsdpError) as ei:
+            call()
+        assert ei.value.code == E.ESDP_ESTATE
+    s.solve_instances()
+    assert s.grad(0, inst.mu0)[0][0] == pytest.approx(J0, rel=1e-6)
+
+
+def test_gradient_in_batch_with_other_ev_path(monkeypatch):
+    """The gradient of one asset of a batch re-sweeps it alone: with four
+    assets its batch tile (40 rows x 64 states) contracts EV on tcgen05 while
+    its own plan (about 8 rows) takes SIMT, so P is prepared again in the
+    SIMT layout; the result equals the gradient from a context of that asset
+    alone (same launch shape, same decisions) to float32 rounding."""
+    insts = [I.random_instance(70 + j, 6, 1200, 64, 20, 20, 1, neg_prob=0.2) for j in range(4)]
+    for inst in insts:
+        inst.s0 = 600
+    monkeypatch.setenv("ESDP_SHAPE", "8,512")
+    s = E.Solver(insts)
+    s.autotune()
+    monkeypatch.delenv("ESDP_SHAPE")
+    assert s.launch_info()["ev"] == "tcgen05"
+    s.solve_instances()
+    a = s.grad(0, insts[0].mu0, extra=True)
+    one = E.Solver([insts[0]])
+    assert one.launch_info()["ev"] == "simt"
+    one.solve_instances()
+    b = one.grad(0, insts[0].mu0, extra=True)
+    for x, y in zip(a, b):
+        x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
+        assert np.abs(x - y).max() <= 1e-5 * max(np.abs(y).max(), 1e-30)
 
 
 # ------------------------------------------------- packed bid curves
