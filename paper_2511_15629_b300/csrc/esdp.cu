@@ -180,18 +180,6 @@ struct AssetChoice {
   int nb, parts, W, n_tiles, rows, rs;
 };
 
-// ESDP_EV = "simt" | "tc" | "mma" pins the EV contraction path where K
-// allows it (so that every path can be exercised on small grids); otherwise
-// the path follows the tile's contraction size (ev_path).
-int ev_force() {
-  const char* f = getenv("ESDP_EV");
-  if (!f) return 0;
-  if (!strcmp(f, "simt")) return 1;
-  if (!strcmp(f, "tc")) return 2;
-  if (!strcmp(f, "mma")) return 3;
-  return 0;
-}
-
 int asset_ev_path(const esdp_asset& a, int W) { return ev_path(W, a.n_modes, a.K, ev_force()); }
 
 size_t smem_need(const esdp_asset& a, const AssetChoice& ch, int R) {

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace esdp {
@@ -68,6 +70,18 @@ __host__ __device__ inline bool tc_shape(int K) { return K >= 16 && K <= 128 && 
 // multiple of 16) or mma.sync (K a multiple of 8).  `force`: 0 automatic;
 // 1 SIMT, 2 tcgen05, 3 mma.sync where K allows it (else SIMT).
 enum EvPath { kEvSimt = 0, kEvTc = 1, kEvMma = 2 };
+
+// The `force` argument from the environment: ESDP_EV = "simt" | "tc" | "mma"
+// pins a path (so that every path can be exercised on small grids); unset or
+// any other value leaves the choice to the tile size.
+inline int ev_force() {
+  const char* f = std::getenv("ESDP_EV");
+  if (!f) return 0;
+  if (!std::strcmp(f, "simt")) return 1;
+  if (!std::strcmp(f, "tc")) return 2;
+  if (!std::strcmp(f, "mma")) return 3;
+  return 0;
+}
 constexpr long long kTensorEvMinWork = 98304;
 inline int ev_path(int W, int M, int K, int force) {
   const bool tc_ok = tc_shape(K), mma_ok = (K & 7) == 0;

@@ -173,8 +173,9 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   d.wait_lo = -reach; d.wait_hi = reach;
   d.t_hi = a.T; d.t_lo = 1; d.ev_keep = 0; d.policy_t_base = 1; d.ckpt_every = 0;
   d.rows = rows; d.rs = rs; d.sw = (float)a.switch_cost;
-  // no prepared P here: a tile large enough for the tensor cores takes mma.sync
-  d.mma = (ev_path(W, M, K, 0) != kEvSimt && (K & 7) == 0) ? 1 : 0;
+  // no prepared P here: where the tile size (or ESDP_EV) picks a tensor path,
+  // mma.sync takes it
+  d.mma = (ev_path(W, M, K, ev_force()) != kEvSimt && (K & 7) == 0) ? 1 : 0;
   d.off_price = d.off_trans = d.off_cost = d.off_terminal = d.off_v1 = 0;
   d.e = reinterpret_cast<const float*>(S + o_e);
   d.v_start = nullptr;

@@ -55,6 +55,33 @@ def test_noalloc_matches_esdp_solve_twice(make):
     s.close()
 
 
+@pytest.mark.parametrize("K", [8, 16])
+def test_noalloc_mma_path(monkeypatch, K):
+    """The mma.sync EV contraction (pinned with ESDP_EV in both entry points,
+    so both take the same arithmetic) gives the regular solve's values and
+    policies."""
+    import torch
+    monkeypatch.setenv("ESDP_EV", "mma")
+    inst = I.random_instance(92 + K, 6, 257, K, 15, 12, 2, neg_prob=0.3)
+    d = _inputs(inst)
+    MNK = inst.n_modes * inst.N * inst.K
+    ref = torch.empty(MNK, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    assert s.launch_info()["ev"] == "mma.sync"
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], ref)
+    ref_pol = torch.empty(inst.T * MNK, dtype=torch.int32, device="cuda")
+    for t in range(1, inst.T + 1):
+        s.policy(0, t, ref_pol[(t - 1) * MNK:t * MNK])
+    torch.cuda.synchronize()
+    V1 = torch.full((MNK,), float("nan"), device="cuda")
+    pol = torch.full((inst.T * MNK,), -7, dtype=torch.int32, device="cuda")
+    E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1, pol)
+    err = float((V1 - ref).abs().max()) / float(ref.abs().max())
+    assert err <= VTOL
+    assert torch.equal(pol, ref_pol)
+    s.close()
+
+
 def test_noalloc_rejects_assets_beyond_the_workspace():
     import torch
     inst = I.random_instance(91, 2, 40000, 64, 3, 3, 1)
