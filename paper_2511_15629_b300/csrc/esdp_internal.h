@@ -56,8 +56,9 @@ struct AssetDev {
   int mma;              // 1: EV contraction on mma.sync m16n8k8 (K a multiple of 8, tc == 0)
 };
 
-// The EV contraction on tcgen05 needs K a multiple of 16 (N of a 128-row MMA)
-// and the prepared operand copy of P.
+// The EV contraction on tcgen05 (64-row MMAs with N = K, k-steps of 8) is
+// built for K a multiple of 16 up to 128 (tensor-memory columns, operand
+// layouts) and needs the prepared operand copy of P.
 __host__ __device__ inline bool tc_shape(int K) { return K >= 16 && K <= 128 && (K & 15) == 0; }
 
 // Unit that contracts EV_{t-1} = P_{t-1} V_t over the rows of a tile of W
