@@ -50,8 +50,12 @@ def assert_policy(gpu, ref, gap, scale, what="policy"):
     return int(((gpu != ref) & ~decided).sum())
 
 
-def solve_gpu(inst, keep_ev=False):
+def solve_gpu(inst, keep_ev=False, tune=False):
+    """Solve on the GPU; tune=True first times the launch shapes as bench.py
+    does, so that the benchmark's launch configuration is the one checked."""
     s = E.Solver([inst], keep_ev=keep_ev)
+    if tune:
+        s.autotune()
     V1 = s.solve_instances()[0]
     return s, V1
 
@@ -60,8 +64,8 @@ def gpu_policies(s, inst):
     return np.stack([s.policy(0, t) for t in range(1, inst.T + 1)])
 
 
-def full_check(inst, keep_ev=False, check_policy=True):
-    s, V1 = solve_gpu(inst, keep_ev=keep_ev)
+def full_check(inst, keep_ev=False, check_policy=True, tune=False):
+    s, V1 = solve_gpu(inst, keep_ev=keep_ev, tune=tune)
     r = O.solve(inst, keep_EV=keep_ev, nthreads=NTHREADS)
     scale = _scale(r["V1"])
     assert_values(V1, r["V1"], scale)
@@ -125,12 +129,12 @@ def test_integer_prices_exact_ties():
 
 
 def test_config2_parity_with_modes():
-    full_check(I.config2(), keep_ev=True)
+    full_check(I.config2(), keep_ev=True, tune=True)
 
 
 def test_config5_values_int16_checkpointed():
     inst = I.config5()
-    s, V1 = solve_gpu(inst)
+    s, V1 = solve_gpu(inst, tune=True)
     r = O.solve(inst, nthreads=NTHREADS, keep_policy=False)
     assert_values(V1, r["V1"], _scale(r["V1"]))
     with pytest.raises(E.EsdpError) as ei:
@@ -167,6 +171,7 @@ def test_config3_full_horizon_sampled_stages():
     from the GPU's own EV_t; V_1 against the full FP64 oracle."""
     inst = I.config3()
     s = E.Solver([inst], keep_ev=True)
+    s.autotune()
     V1 = s.solve_instances()[0]
     for t in (inst.T, 1500, 700, 2):
         ev_t = s.expected_value(0, t).astype(np.float64)
@@ -257,8 +262,8 @@ def _gpu_full_policy(inst):
     return gpu_policies(s, full).astype(np.int32)
 
 
-def _grad_check(inst, tie_free):
-    s, V1 = solve_gpu(inst)
+def _grad_check(inst, tie_free, tune=False):
+    s, V1 = solve_gpu(inst, tune=tune)
     J, dp, dt, de, dco, dsw, dterm, dmu = s.grad(0, inst.mu0, extra=True)
     r = O.solve(inst, keep_V=True, nthreads=NTHREADS)
     scale = _scale(r["V1"])
@@ -323,7 +328,7 @@ def test_gradient_repeat_calls_agree():
 
 
 def test_gradient_config5():
-    n = _grad_check(I.config5(), tie_free=False)
+    n = _grad_check(I.config5(), tie_free=False, tune=True)
     print(f"config5: {n} near-tie decisions differ from the FP64 oracle's")
 
 
