@@ -199,8 +199,9 @@ int esdp_status(esdp_ctx* ctx, void* stream);
 /* Counters of the chosen launch shape: grid, block, work items, rows per
  * tile of asset 0, actions split (parts), R (rows per thread), and the unit
  * that contracts EV for asset 0 (ev_path: 0 FP32 SIMT, 1 tcgen05 split-tf32,
- * 2 mma.sync split-tf32; tiles of at least 98,304 multiply-adds per stage,
- * rows x modes x K^2, take a tensor path when K is a multiple of 16 resp. 8;
+ * 2 mma.sync split-tf32; tiles with K >= 64 and at least 98,304
+ * multiply-adds per stage, rows x modes x K^2, take a tensor path when K is
+ * a multiple of 16 resp. 8;
  * the environment variable ESDP_EV = "simt" | "tc" | "mma" pins one where K
  * allows it).  Any pointer may be NULL. */
 int esdp_launch_info(const esdp_ctx* ctx, int32_t* grid, int32_t* block, int32_t* items,

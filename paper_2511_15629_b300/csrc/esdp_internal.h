@@ -64,12 +64,14 @@ __host__ __device__ inline bool tc_shape(int K) { return K >= 16 && K <= 128 && 
 // Unit that contracts EV_{t-1} = P_{t-1} V_t over the rows of a tile of W
 // rows x M modes x K states (W M K^2 multiply-adds per stage).  The tensor
 // paths repay their fixed cost (the tf32 operand split, MMA issue and
-// completion, the read-back) only on large tiles: on B300, FP32 SIMT was the
-// faster for 16-row tiles at K = 16..64 (W M K^2 <= 65,536, by 4-11 %) and
-// tcgen05 for 36-row tiles at K = 64 (147,456, by 8 %; mma.sync 2.6 % ahead
-// of SIMT there), so tiles from 98,304 multiply-adds take tcgen05 (K a
-// multiple of 16) or mma.sync (K a multiple of 8).  `force`: 0 automatic;
-// 1 SIMT, 2 tcgen05, 3 mma.sync where K allows it (else SIMT).
+// completion, the read-back) only on large contractions with many states:
+// on B300, FP32 SIMT was the faster for 16-row tiles at K = 16..64
+// (W M K^2 <= 65,536, by 4-11 %) and for the 256-asset batch with K = 8..40
+// on tiles of up to hundreds of rows (by 1.5 %), tcgen05 for 36-row tiles at
+// K = 64 (147,456, by 8 %; mma.sync 2.6 % ahead of SIMT there).  So tiles
+// with K >= 64 and from 98,304 multiply-adds take tcgen05 (K a multiple of
+// 16) or mma.sync (K a multiple of 8).  `force`: 0 automatic; 1 SIMT,
+// 2 tcgen05, 3 mma.sync where K allows it (else SIMT).
 enum EvPath { kEvSimt = 0, kEvTc = 1, kEvMma = 2 };
 
 // The `force` argument from the environment: ESDP_EV = "simt" | "tc" | "mma"
@@ -84,12 +86,13 @@ inline int ev_force() {
   return 0;
 }
 constexpr long long kTensorEvMinWork = 98304;
+constexpr int kTensorEvMinK = 64;
 inline int ev_path(int W, int M, int K, int force) {
   const bool tc_ok = tc_shape(K), mma_ok = (K & 7) == 0;
   if (force == 1) return kEvSimt;
   if (force == 2) return tc_ok ? kEvTc : kEvSimt;
   if (force == 3) return mma_ok ? kEvMma : kEvSimt;
-  if ((long long)W * M * K * K < kTensorEvMinWork) return kEvSimt;
+  if (K < kTensorEvMinK || (long long)W * M * K * K < kTensorEvMinWork) return kEvSimt;
   return tc_ok ? kEvTc : (mma_ok ? kEvMma : kEvSimt);
 }
 

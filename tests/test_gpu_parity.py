@@ -580,20 +580,24 @@ def test_ev_path_parity(monkeypatch, path, K, M):
     assert_values(ev, r["EV"], scale, "EV")
 
 
-@pytest.mark.parametrize("N,K,M", [(5001, 64, 1), (2001, 32, 1), (5001, 56, 2), (2001, 24, 2),
-                                   (1001, 128, 1), (301, 16, 2)])
-def test_ev_path_follows_tile_work(N, K, M):
-    """Without a pin the EV unit follows the contraction work of a tile,
-    rows x modes x K^2: from 98,304 multiply-adds tcgen05 (K a multiple of
-    16) or mma.sync (K a multiple of 8), below it FP32 SIMT."""
+@pytest.mark.parametrize("N,K,M,want", [(5001, 64, 1, "tcgen05"), (5001, 72, 1, "mma.sync"),
+                                        (2001, 64, 1, None), (5001, 56, 1, "simt"),
+                                        (2001, 32, 1, "simt"), (1001, 128, 1, None),
+                                        (301, 16, 2, "simt")])
+def test_ev_path_follows_tile_work(N, K, M, want):
+    """Without a pin the EV unit follows the contraction of a tile: with
+    K >= 64 and at least 98,304 multiply-adds (rows x modes x K^2) tcgen05
+    (K a multiple of 16) or mma.sync (K a multiple of 8), else FP32 SIMT."""
     inst = I.random_instance(600 + K, 3, N, K, 100, 100, M)
     s = E.Solver([inst])
     info = s.launch_info()
     work = info["rows_per_tile"] * M * K * K
-    want = "simt"
-    if work >= 98304:
-        want = "tcgen05" if K % 16 == 0 else ("mma.sync" if K % 8 == 0 else "simt")
-    assert info["ev"] == want
+    rule = "simt"
+    if K >= 64 and work >= 98304:
+        rule = "tcgen05" if K % 16 == 0 else ("mma.sync" if K % 8 == 0 else "simt")
+    assert info["ev"] == rule
+    if want is not None:  # else the tile size decides either way
+        assert rule == want, f"tile of {info['rows_per_tile']} rows"
     s.close()
 
 
