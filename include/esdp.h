@@ -177,6 +177,9 @@ int esdp_objective(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, vo
  *   d_switch   [1]         double  dJ/dswitch_cost (0 with one mode)
  *   d_terminal [n_modes*N*K] float dJ/dterminal = the occupancy after stage T
  *   d_mu0      [K]         float   dJ/dmu0[k] = V_1[0][s0][k]
+ * Repeated calls on the same solve give the same bits (the occupancy is
+ * scattered in 64-bit fixed point, 2^-32 units; ESDP_ENUMERIC if an
+ * occupancy entry exceeds 2^20, e.g. from a mu0 far from a distribution).
  * Device or host pointers as the context's flags say; blocks until done. */
 int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* d_price,
               float* d_trans, double* d_eta, float* d_cost, double* d_switch, float* d_terminal,

@@ -72,6 +72,7 @@ struct esdp_ctx {
   std::vector<void*> allocs;
   float* d_e = nullptr;           // concatenated action energies
   std::vector<long long> off_e;
+  std::vector<float> fx_e;        // per asset: fixed-point scale of rho * e_a in the adjoint
   std::vector<float*> d_ev;       // per asset
   std::vector<void*> d_policy;    // per asset (full policy) or nullptr
   std::vector<float*> d_ckpt;     // per asset or nullptr
@@ -447,7 +448,9 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
   sp.sm_A2 = p->sm_A2;
   sp.tmem_cols = p->tmem_cols;
   CK(cudaMemsetAsync(p->d_flags, 0, std::max(1, p->n_flags) * sizeof(int), st), "reset flags");
-  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "reset status");
+  // a gradient's segment re-sweeps keep the status word of the whole call
+  // (reset once by esdp_grad), so an earlier segment's error is not lost
+  if (!d_assets) CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "reset status");
   if (prep) {
     CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
     for (size_t j = 0; j < p->adev.size(); ++j) c->prep_tc[p->asset_ids[j]] = p->adev[j].tc;
@@ -631,6 +634,12 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
       if (d > 0) en = -(double)d * delta / a.eta_c;
       e[c->off_e[id] + j] = (float)en;
     }
+    // 2^(32 - ceil(log2 max|e_a|)): |rho e_a| in these units stays below |rho| 2^32
+    float emax = 0.f;
+    for (int j = 0; j < a.A; ++j) emax = std::max(emax, std::fabs(e[c->off_e[id] + j]));
+    int ex = 0;
+    if (emax > 0.f) std::frexp(emax, &ex);
+    c->fx_e.push_back(std::ldexp(1.f, 32 - ex));
   }
   if ((rc = dalloc(c, &c->d_e, e.size()))) return rc;
   CK(cudaMemcpy(c->d_e, e.data(), e.size() * sizeof(float), cudaMemcpyHostToDevice), "copy e");
@@ -1077,7 +1086,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   }
   // workspace: carved from the context's gradient scratch (kept across calls)
   void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
-      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs, *dtpart, *dtmass;
+      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs, *dtpart, *dtmass, *post_fx;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
   const int MN = M * N;
   int ogrid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));  // occupancy CTAs
@@ -1086,14 +1095,14 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   {
     void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
                      &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
-                     &opart_acc, &dsegs, &dtpart, &dtmass};
+                     &opart_acc, &dsegs, &dtpart, &dtmass, &post_fx};
     const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
                             (size_t)T * K * 8, 8 * 8, (size_t)ogrid * 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
                             (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
                             (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
                             (size_t)nseg * sizeof(AssetDev), (size_t)C * 4 * K * K * 8,
-                            (size_t)C * 4 * K * 8};
+                            (size_t)C * 4 * K * 8, L * C * 8};
     size_t total = 0;
     for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
     if (total > c->grad_scr_bytes) {
@@ -1108,7 +1117,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
       c->grad_scr_bytes = total;
     }
     char* q = (char*)c->grad_scr;
-    for (int i = 0; i < 20; ++i) {
+    for (int i = 0; i < 21; ++i) {
       *outs[i] = q;
       q += (sizes[i] + 255) / 256 * 256;
     }
@@ -1122,6 +1131,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   if ((e = cudaMemcpyAsync(d_mu, mu0, K * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            st)) != cudaSuccess)
     return cfail(e, "mu0 copy");
+  cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
   cudaMemsetAsync(rho, 0, L * 4, st);
   cudaMemsetAsync(dprice64, 0, (size_t)T * K * 8, st);
   cudaMemsetAsync(acc, 0, 64, st);
@@ -1178,7 +1188,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     if ((e = cudaMemcpyAsync((float*)seg_v + (size_t)nt * L, vend, L * 4, cudaMemcpyDeviceToDevice,
                              st)) != cudaSuccess)
       return cfail(e, "segment copy");
-    cudaMemsetAsync(seg_post, 0, L * nt * 4, st);
+    cudaMemsetAsync(post_fx, 0, L * nt * 8, st);
     cudaMemsetAsync(bar, 0, (size_t)ogrid * 4, st);
     OccParams op{};
     op.N = N; op.K = K; op.M = M; op.A = a.A; op.D_dis = a.D_dis;
@@ -1197,6 +1207,8 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.policy_bytes = pb;
     op.rho = (float*)rho;
     op.post = (float*)seg_post;
+    op.post_fx = (unsigned long long*)post_fx;
+    op.fx_e = c->fx_e[asset];
     op.d_price = (double*)dprice64;
     op.acc = (double*)acc;
     op.d_cost = (double*)dcost64;

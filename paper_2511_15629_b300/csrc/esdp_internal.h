@@ -247,7 +247,9 @@ struct OccParams {
   const void* policy;     // stages t_lo..t_hi, [C][M][N][K]
   int policy_bytes;
   float* rho;             // [M][N][K], holds rho_{t_lo} on entry, rho_{t_hi+1} on exit
-  float* post;            // [C][M][N][K], zero on entry
+  float* post;            // [C][M][N][K], written by the kernel
+  unsigned long long* post_fx;  // [C][M][N][K] the scatter's fixed-point sums, zero on entry
+  float fx_e;             // fixed-point scale (a power of two) of the rho * e_a terms
   double* d_price;        // [T][K] (accumulated)
   double* acc;            // [5]: d_eta_c, d_eta_d, (two unused slots), d_switch
   double* d_cost;         // [A] (accumulated)

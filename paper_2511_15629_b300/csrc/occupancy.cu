@@ -21,6 +21,14 @@
 // flags and bounded acquire polls); dtrans_kernel then forms dJ/dP for the segment from
 // the stored post-decision occupancies and values (a split-row reduction per
 // stage and 32 x 32 output tile).
+//
+// The scatter adds with atomics, in 64-bit fixed point: integer addition is
+// associative, so the sums do not depend on the order in which threads and
+// CTAs arrive, and every other sum runs in a fixed order, so the gradients
+// are the same bit for bit on every call.  Occupancy mass is counted in
+// units of 2^-32 (entries up to 2^20 are accepted, sums must stay below
+// 2^31), the rho * e_a terms of dJ/dprice in units chosen from the largest
+// |e_a| so that they have the same range.
 #include <cuda_runtime.h>
 
 #include "../../include/esdp.h"
@@ -109,14 +117,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+constexpr float kFxRho = 4294967296.f;  // 2^32 units per unit of occupancy mass
+constexpr double kFxRhoInv = 1.0 / 4294967296.0;
+constexpr float kFxMaxRho = 1048576.f;  // 2^20: larger entries are reported
+
+__device__ __forceinline__ unsigned long long to_fx(float x, float scale) {
+  return (unsigned long long)__float2ll_rn(x * scale);  // scale: a power of two
+}
+
 __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
-  // float32 per-state terms and shared sums (few terms each: this part's FP64
-  // pipe is 64x slower than FP32), double from the per-warp sums on
+  // float32 per-state terms (few terms each: this part's FP64 pipe is 64x
+  // slower than FP32), fixed-point shared sums, double from the warp sums on
   extern __shared__ double osm[];
-  double* sacc = osm;                                       // [8] warp-sum accumulators
-  float* sk = reinterpret_cast<float*>(osm + 8);            // [K] dprice partials
-  float* sc = sk + p.K;                                     // [A] cost partials (segment)
-  float* Ps = sc + p.A;                                     // [K][K]
+  double* sacc = osm;                                       // [8] segment accumulators
+  double* wacc = osm + 8;                                   // [8 warps][3] stage warp sums
+  unsigned long long* skx = reinterpret_cast<unsigned long long*>(osm + 32);  // [K] dprice
+  unsigned long long* scx = skx + p.K;                      // [A] cost partials (segment)
+  float* Ps = reinterpret_cast<float*>(scx + p.A);          // [K][K]
   __shared__ int s_abort;
   const int K = p.K, N = p.N, M = p.M, MN = M * N;
   const size_t MNK = (size_t)MN * K;
@@ -126,19 +143,20 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   // d rho lam delta / eta_c^2 per charging step, d rho lam delta per discharging step
   const float coef_c = (float)(p.delta / (p.eta_c * p.eta_c)), coef_d = (float)p.delta;
   if (tid == 0) s_abort = 0;
-  for (int a = tid; a < p.A; a += nth) sc[a] = 0.f;
+  for (int a = tid; a < p.A; a += nth) scx[a] = 0ull;
   if (tid < 8) sacc[tid] = 0.0;  // summed over the segment
   __syncthreads();
   int epoch = 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
-    for (int i = tid; i < K; i += nth) sk[i] = 0.f;
+    for (int i = tid; i < K; i += nth) skx[i] = 0ull;
     {  // P_t for the contraction: its load overlaps the scatter
       const float* P = p.trans + (size_t)(t - 1) * K * K;
       for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
     }
     __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
+    unsigned long long* post_fx = p.post_fx + (size_t)ts * MNK;
     const float* price_t = p.price + (size_t)(t - 1) * K;
     float dc = 0.f, dd = 0.f, dsw = 0.f;
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
@@ -150,17 +168,18 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       const int a = p.policy_bytes == 2 ? (int)reinterpret_cast<const short*>(p.policy)[pi]
                                         : reinterpret_cast<const int*>(p.policy)[pi];
       const int d = a - p.D_dis;
-      if (a < 0 || a >= p.A || s + d < 0 || s + d >= N) {  // not a feasible stored action
+      if (a < 0 || a >= p.A || s + d < 0 || s + d >= N ||  // not a feasible stored action,
+          !(fabsf(rho) <= kFxMaxRho)) {                     // or outside the fixed-point range
         atomicCAS(p.status, 0, ESDP_ENUMERIC);
         continue;
       }
       const int m2 = (M == 2) ? (d < 0 ? 0 : (d > 0 ? 1 : m)) : 0;
-      atomicAdd(post + ((size_t)m2 * N + s + d) * K + k, rho);
+      atomicAdd(post_fx + ((size_t)m2 * N + s + d) * K + k, to_fx(rho, kFxRho));
       const float lam = price_t[k];
-      atomicAdd(&sk[k], rho * p.e[a]);
+      atomicAdd(&skx[k], to_fx(rho * p.e[a], p.fx_e));
       if (d > 0) dc = fmaf(rho * lam, (float)d * coef_c, dc);
       if (d < 0) dd = fmaf(rho * lam, (float)(-d) * coef_d, dd);
-      atomicAdd(&sc[a], -rho);
+      atomicAdd(&scx[a], to_fx(-rho, kFxRho));
       if (M == 2 && m == 1 && d < 0) dsw -= rho;
     }
 #pragma unroll
@@ -170,24 +189,35 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       dsw += __shfl_xor_sync(0xffffffffu, dsw, o);
     }
     if ((tid & 31) == 0) {
-      atomicAdd(&sacc[0], (double)dc);
-      atomicAdd(&sacc[1], (double)dd);
-      atomicAdd(&sacc[4], (double)dsw);
+      wacc[(tid >> 5) * 3 + 0] = (double)dc;
+      wacc[(tid >> 5) * 3 + 1] = (double)dd;
+      wacc[(tid >> 5) * 3 + 2] = (double)dsw;
     }
     __syncthreads();
     // this CTA's partials of the stage (and, once, of the segment's costs
     // and accumulators): plain stores, added up after the launch in a fixed
-    // order
-    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
-    for (int i = tid; i < K; i += nth) pr[i] = (double)sk[i];
-    if (t == p.t_hi) {
-      for (int a = tid; a < p.A; a += nth)
-        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)sc[a];
-      if (tid < 8) p.part_acc[(size_t)blockIdx.x * 8 + tid] = sacc[tid];
+    // order; the warp sums are added in warp order
+    if (tid == 0) {
+      for (int wq = 0; wq < (nth >> 5); ++wq) {
+        sacc[0] += wacc[wq * 3 + 0];
+        sacc[1] += wacc[wq * 3 + 1];
+        sacc[4] += wacc[wq * 3 + 2];
+      }
+      if (t == p.t_hi)
+        for (int q = 0; q < 8; ++q) p.part_acc[(size_t)blockIdx.x * 8 + q] = sacc[q];
     }
+    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
+    for (int i = tid; i < K; i += nth) pr[i] = (double)(long long)skx[i] / (double)p.fx_e;
+    if (t == p.t_hi)
+      for (int a = tid; a < p.A; a += nth)
+        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)(long long)scx[a] * kFxRhoInv;
     ++epoch;
     publish_stage(p.flags, epoch);
     if (!wait_sources(p, r0, r1, epoch, &s_abort)) return;
+    // own rows of the post-decision occupancy, complete: fixed point to float
+    for (int i = r0 * K + tid; i < r1 * K; i += nth)
+      post[i] = (float)((double)(long long)__ldcg(post_fx + i) * kFxRhoInv);
+    __syncthreads();
     // contraction of the post-decision occupancy with P_t (own rows)
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const int row = i / K, k2 = i - row * K;
@@ -357,7 +387,9 @@ cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream)
 }
 
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream) {
-  const size_t smem = 8 * sizeof(double) + (size_t)(p.K + p.A + p.K * p.K) * sizeof(float);
+  // segment sums, 8 warps x 3 stage sums, fixed-point K + A sums, P_t
+  const size_t smem = 32 * sizeof(double) + (size_t)(p.K + p.A) * sizeof(unsigned long long) +
+                      (size_t)p.K * p.K * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(occ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

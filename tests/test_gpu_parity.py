@@ -310,10 +310,9 @@ def test_gradient_modes_checkpointed():
 
 
 def test_gradient_repeat_calls_agree():
-    """Two gradient calls on the same solve agree to float32 rounding (the
-    occupancy scatter adds with atomics, so the order of its float sums, and
-    with it the last bits, may differ between calls; the cross-CTA sums are
-    in a fixed order)."""
+    """Two gradient calls on the same solve give the same bits: the
+    occupancy scatter adds in fixed point (associative integer atomics) and
+    every other sum runs in a fixed order."""
     inst = I.random_instance(55, 30, 150, 6, 10, 12, 2, neg_prob=0.2, switch_cost=3.0)
     inst.s0 = 70
     inst.ckpt_every = 8
@@ -322,9 +321,21 @@ def test_gradient_repeat_calls_agree():
     a = s.grad(0, mu0, extra=True)
     b = s.grad(0, mu0, extra=True)
     for x, y in zip(a, b):
-        x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
-        scale = max(np.abs(x).max(), 1e-30)
-        assert np.abs(x - y).max() <= 1e-5 * scale
+        np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_gradient_rejects_occupancy_beyond_fixed_point_range():
+    """An initial distribution with entries above 2^20 cannot be added in the
+    scatter's fixed point: the call reports ESDP_ENUMERIC instead of
+    wrapping around."""
+    inst = I.random_instance(56, 6, 80, 4, 5, 5, 1)
+    inst.s0 = 40
+    s, _ = solve_gpu(inst)
+    with pytest.raises(E.EsdpError) as ei:
+        s.grad(0, np.full(inst.K, 4.0e6, np.float32))
+    assert ei.value.code == E.ESDP_ENUMERIC
+    J = s.grad(0, inst.mu0)[0]  # the context stays usable
+    assert np.isfinite(J).all()
 
 
 def test_gradient_config5():
