@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   unsigned long long* skx = reinterpret_cast<unsigned long long*>(osm + 32);  // [K] dprice
   unsigned long long* scx = skx + p.K;                      // [A] cost partials (segment)
   float* Ps = reinterpret_cast<float*>(scx + p.A);          // [K][K]
+  float* spost = Ps + p.K * p.K;  // [grid_rows][K] own converted rows (if own_smem)
   __shared__ int s_abort;
   const int K = p.K, N = p.N, M = p.M, MN = M * N;
   const size_t MNK = (size_t)MN * K;
@@ -214,16 +215,25 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     ++epoch;
     publish_stage(p.flags, epoch);
     if (!wait_sources(p, r0, r1, epoch, &s_abort)) return;
-    // own rows of the post-decision occupancy, complete: fixed point to float
-    for (int i = r0 * K + tid; i < r1 * K; i += nth)
-      post[i] = (float)((double)(long long)__ldcg(post_fx + i) * kFxRhoInv);
+    // own rows of the post-decision occupancy, complete: fixed point to
+    // float, for dJ/dP and (in shared memory when they fit) the contraction
+    for (int i = r0 * K + tid; i < r1 * K; i += nth) {
+      const float v = (float)((double)(long long)__ldcg(post_fx + i) * kFxRhoInv);
+      post[i] = v;
+      if (p.own_smem) spost[i - r0 * K] = v;
+    }
     __syncthreads();
     // contraction of the post-decision occupancy with P_t (own rows)
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
       const int row = i / K, k2 = i - row * K;
-      const float* pr = post + (size_t)row * K;
       float acc = 0.f;
-      for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(pr + k), Ps[k * K + k2], acc);
+      if (p.own_smem) {
+        const float* pr = spost + (size_t)(row - r0) * K;
+        for (int k = 0; k < K; ++k) acc = fmaf(pr[k], Ps[k * K + k2], acc);
+      } else {
+        const float* pr = post + (size_t)row * K;
+        for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(pr + k), Ps[k * K + k2], acc);
+      }
       p.rho[i] = acc;
     }
     __syncthreads();
@@ -387,13 +397,17 @@ cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream)
 }
 
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream) {
-  // segment sums, 8 warps x 3 stage sums, fixed-point K + A sums, P_t
-  const size_t smem = 32 * sizeof(double) + (size_t)(p.K + p.A) * sizeof(unsigned long long) +
+  // segment sums, 8 warps x 3 stage sums, fixed-point K + A sums, P_t, and
+  // the own converted rows when they fit
+  const size_t base = 32 * sizeof(double) + (size_t)(p.K + p.A) * sizeof(unsigned long long) +
                       (size_t)p.K * p.K * sizeof(float);
+  const size_t own = (size_t)p.grid_rows * p.K * sizeof(float);
+  OccParams pp = p;
+  pp.own_smem = base + own <= 160 * 1024 ? 1 : 0;
+  const size_t smem = base + (pp.own_smem ? own : 0);
   cudaError_t e = cudaFuncSetAttribute(occ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  OccParams pp = p;
   void* args[] = {&pp};
   return cudaLaunchCooperativeKernel((const void*)occ_kernel, dim3(grid), dim3(block), args, smem,
                                      stream);
