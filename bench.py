@@ -1,13 +1,18 @@
 """Benchmark: Bellman action evaluations per second of the storage DP.
 
-One step = one pass of the whole hot path over the 5-minute real-time
-workload (T=288, N=1001, K=20, A=201, two modes): the persistent
-backward-induction sweep (EV contraction + banded max-plus + argmax policy,
-all stages in one launch) followed by the convexified bid curves of every
-(t, mode, k).  Inputs are synthetic (seeded generators).
+One step = one pass of the hot path over the large single-asset workload
+(one week of 5-minute stages: T=2016, N=5001 SoC points, K=64 price states
+with dense per-stage transition matrices, A=201 actions): the persistent
+backward-induction sweep -- row sums and operand preparation of P, then one
+launch that runs every stage's EV contraction (tcgen05), banded max-plus and
+argmax policy (int32, kept in HBM).  Inputs are synthetic (seeded
+generators) and resident in HBM before the timed region.  The other
+workloads (the two-mode 5-minute asset with its bid curves, the 256-asset
+portfolio, the adjoint, the small day-ahead case, the paper's Table III
+shapes) are reported under "extra".
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
-oracle on the same workload instead.
+oracle on bounded samples of the same workload instead.
 """
 from __future__ import annotations
 
@@ -25,8 +30,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Bellman evals/s (T*N*K*A / sweep s)"
-WORKLOAD = "config2: T=288 N=1001 K=20 A=201 modes=2, sweep + bid curves of every (t,m,k)"
+WORKLOAD = ("config3: T=2016 N=5001 K=64 A=201, one asset, dense per-stage transitions; "
+            "persistent sweep with the int32 argmax policy kept")
 UNIT = "evals/s"
+# stages of the workload the CPU oracle takes per timed sample (the last ones)
+REF_SAMPLE_STAGES = 16
+CPU_BASELINE_STAGES = 256
+
+
+def step_config():
+    """The `config` of both arms' JSON lines (identical, so that they compare)."""
+    from paper_2511_15629_b300 import instances as I
+    inst = I.config3()
+    return inst, {"workload": WORKLOAD, "evals_per_step": inst.evals,
+                  "l2": "flushed between timed GPU steps (512 MB write)",
+                  "parallelism": "one GPU per replica"}
 
 
 def parse():
@@ -37,9 +55,12 @@ def parse():
     ap.add_argument("--impl", choices=["esdp", "reference"], default="esdp")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the large-asset, portfolio and adjoint sub-benchmarks")
-    ap.add_argument("--only", default="", help="run one sub-benchmark: config3|config4|config5")
+    ap.add_argument("--only", default="", help="run one sub-benchmark (a key of EXTRAS)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--phase-clocks", action="store_true",
+                    help="per-stage cycles of each sweep phase (config3 and config2) from the "
+                         "library built with per-phase clock counters; prints one JSON line")
     ap.add_argument("--profile-case", default="",
                     help="config3-64 | config2 | table3-20h: one solve inside the NVTX range 'esdp_profile' "
                          "(for ncu --nvtx --nvtx-include esdp_profile/)")
@@ -135,11 +156,14 @@ def measured_peaks() -> dict:
     return {}
 
 
-def measured_traffic():
-    """DRAM bytes per sweep launch from the committed ncu capture, or None
+def measured_traffic(name):
+    """DRAM bytes of one full sweep launch from a committed ncu capture
+    (`profiles/<name>`): read + write bytes of the captured launch, scaled
+    by the record's `scale` when the capture ran a shorter horizon of the
+    same asset (the traffic is per stage, mostly the streamed policy).  None
     when the kernel source has changed since the counters were taken."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic_config2.json")
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -147,7 +171,7 @@ def measured_traffic():
     with open(os.path.join(ROOT, rec["source"]), "rb") as f:
         if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
             return None
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * float(rec.get("scale", 1.0))
 
 
 def alu_peak_evals(n_sm: int, mhz: float) -> float:
@@ -174,19 +198,29 @@ def host_cores() -> int:
 
 # --------------------------------------------------------------- reference
 
+def tail_instance(inst, n):
+    """The last n stages of an instance (same grid, terminal and actions)."""
+    import copy
+    part = copy.copy(inst)
+    part.T = n
+    part.price = np.ascontiguousarray(inst.price[-n:])
+    part.trans = np.ascontiguousarray(inst.trans[-n:])
+    return part
+
+
 def run_reference(args, rank):
-    """FP64 CPU oracle on the same step: full solve (policy kept) + the
-    envelope of every (t, m, k)."""
+    """FP64 CPU oracle on the GPU arm's workload: each step is a bounded
+    sample, the backward induction (policy kept) over the last
+    REF_SAMPLE_STAGES stages, on every host core; evals/s of the sample."""
     if rank != 0:
         return
     from oracle import oracle as O
-    from paper_2511_15629_b300 import instances as I
-    inst = I.config2()
+    inst, config = step_config()
     cores = host_cores()
+    part = tail_instance(inst, REF_SAMPLE_STAGES)
 
     def step():
-        r = O.solve(inst, keep_EV=True, nthreads=cores)
-        O.bid_curves(inst, r["EV"])
+        O.solve(part, nthreads=cores)
 
     for _ in range(args.warmup):
         step()
@@ -194,45 +228,43 @@ def run_reference(args, rank):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    value = inst.evals * args.steps / dt
+    value = part.evals * args.steps / dt
+    sample = (f"{args.steps} samples of the last {REF_SAMPLE_STAGES} stages each "
+              f"({part.evals:.3e} evaluations), FP64 solve with policy, {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "evals_per_step": inst.evals,
-                   "parallelism": f"cpu ({cores} threads)"},
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full steps (solve + envelopes)"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 # -------------------------------------------------------------- GPU arm
 
-def cpu_baseline_c2():
-    """The oracle as it stands, one full config2 step on all host cores."""
+def cpu_baseline_c3():
+    """The oracle as it stands, on a bounded sample of the workload: the last
+    CPU_BASELINE_STAGES stages on all host cores, and the last 4 stages on
+    one thread."""
     from oracle import oracle as O
-    from paper_2511_15629_b300 import instances as I
-    inst = I.config2()
+    inst, _ = step_config()
     cores = host_cores()
+    part = tail_instance(inst, CPU_BASELINE_STAGES)
     t0 = time.perf_counter()
-    r = O.solve(inst, keep_EV=True, nthreads=cores)
-    O.bid_curves(inst, r["EV"])
+    O.solve(part, nthreads=cores)
     dt = time.perf_counter() - t0
-    # the same oracle on one thread, on the first 48 stages (a bounded sample)
-    import copy
-    part = copy.copy(inst)
-    part.T = 48
-    part.price, part.trans = inst.price[:48].copy(), inst.trans[:48].copy()
+    one = tail_instance(inst, 4)
     t1 = time.perf_counter()
-    O.solve(part, nthreads=1)
+    O.solve(one, nthreads=1)
     dt1 = time.perf_counter() - t1
-    return {"value": inst.evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "one full config2 step (FP64 solve with policy + 11520 envelopes), "
-                      f"{dt:.1f} s",
-            "single_thread": {"value": part.evals / dt1, "unit": UNIT, "cores": 1,
-                              "sample": f"config2 stages 1-48, FP64 solve with policy, {dt1:.1f} s"}}
+    return {"value": part.evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"config3 stages {inst.T - CPU_BASELINE_STAGES + 1}-{inst.T}: FP64 solve "
+                      f"with policy, {part.evals:.3e} evaluations in {dt:.1f} s",
+            "single_thread": {"value": one.evals / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"config3 stages {inst.T - 3}-{inst.T}, FP64 solve with "
+                                        f"policy, {dt1:.1f} s"}}
 
 
 def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
@@ -256,6 +288,24 @@ def time_steps(torch, step, steps, warmup, stream, flush, marks=1):
     return sum(per_mark), per_mark
 
 
+def time_steps_with(torch, step, steps, warmup, stream, flush, after_each):
+    """time_steps with a host callback after each timed step (run after the
+    step's events, outside them)."""
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    torch.cuda.nvtx.range_push("esdp_steps")
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush()
+            step(ev[i])
+        after_each()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    return sum(ev[i][0].elapsed_time(ev[i][1]) / 1e3 for i in range(steps)), None
+
+
 def run_esdp(args, rank, world):
     import torch
     from paper_2511_15629_b300 import dist as D
@@ -276,19 +326,16 @@ def run_esdp(args, rank, world):
             print(json.dumps({"extra": extras}), flush=True)
         return
 
-    # ---- the main workload (config2 step: sweep + bid curves)
-    inst = I.config2()
+    # ---- the main workload: the config3 sweep (policy kept)
+    inst, config = step_config()
     cat = E.concat_inputs([inst])
     d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
     MNK = inst.n_modes * inst.N * inst.K
     V1 = torch.empty(MNK, device="cuda")
-    nh = inst.T * inst.n_modes * inst.K
-    n_bp = torch.empty(nh, dtype=torch.int32, device="cuda")
-    idx = torch.empty(nh * inst.N, dtype=torch.int32, device="cuda")
-    slope = torch.empty(nh * inst.N, dtype=torch.float32, device="cuda")
-    s = E.Solver([inst], device_ptrs=True, keep_ev=True)
+    s = E.Solver([inst], device_ptrs=True, time_sweep=True)
     s.autotune(stream=stream)
     torch.cuda.synchronize()
+    sweep_ms = []
 
     def step(evs):
         st = torch.cuda.current_stream()
@@ -297,49 +344,48 @@ def run_esdp(args, rank, world):
         s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
         if evs:
             evs[1].record(st)
-        s.bid_curves(0, 1, inst.T + 1, n_bp, idx, slope, stream=st)
-        if evs:
-            evs[2].record(st)
+            sweep_ms.append(None)   # filled after the timed region
 
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        total, (t_sweep, t_hull) = time_steps(torch, step, args.steps, args.warmup, stream,
-                                              flush, marks=2)
+        total, _ = time_steps_with(torch, step, args.steps, args.warmup, stream, flush,
+                                   after_each=lambda: sweep_ms.__setitem__(-1, s.sweep_ms()))
     torch.cuda.synchronize()
     assert s.status(stream=stream) == 0, "device status after the timed steps"
     total = D.job_seconds(total, torch, device="cuda")  # max over ranks
     value = D.aggregate_rate(inst.evals * args.steps, world, total)
+    t_sweep = sum(sweep_ms) / 1e3
     sweep_evals_s = inst.evals * args.steps / t_sweep
     peak = alu_peak_evals(n_sm, f_max)
     clocks = clk.summary()
     roof = {"bound": "alu", "achieved": sweep_evals_s / 1e9, "peak": peak / 1e9,
-            "unit": "Gevals/s", "frac": sweep_evals_s / peak, "traffic": measured_traffic(),
-            "kernel": "sweep_kernel", "peak_basis": f"{n_sm} SMs x 128 lane-instructions x "
-            f"{f_max:.0f} MHz, one lane-instruction per evaluation (packed add + 3-input max; "
-            "max clock)"}
+            "unit": "Gevals/s", "frac": sweep_evals_s / peak,
+            "traffic": measured_traffic("traffic_config3.json"),
+            "kernel": "sweep_kernel", "launch_ms": t_sweep / args.steps * 1e3,
+            "algorithmic_per_launch": f"{inst.evals:.4e} evaluations (T*N*K*A)",
+            "peak_basis": f"{n_sm} SMs x 128 lane-instructions x {f_max:.0f} MHz (max clock), one "
+            "lane-instruction per evaluation (packed add + 3-input max); of measured issue "
+            "rates (alu_probe)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = sweep_evals_s / alu_peak_evals(n_sm, clocks["sm_mhz"])
     info = s.launch_info()
+    s.close()
+    del d, V1
 
-    # ---- end to end through the host-pointer API (pinned host buffers)
+    # ---- end to end through the host-pointer API (pinned host buffers):
+    # inputs copied in, the sweep, V_1 copied back, every step
     e2e = None
     if not args.no_e2e:
         pin = {k: torch.from_numpy(v).pin_memory() for k, v in cat.items()}
         hp = {k: v.numpy() for k, v in pin.items()}
         hV1 = torch.empty(MNK, dtype=torch.float32).pin_memory().numpy()
-        # bid curves in packed form: offsets plus each envelope's vertices and
-        # slopes, so that the read-back is the vertices, not N-long rows
-        hoff = torch.empty(nh + 1, dtype=torch.int64).pin_memory().numpy()
-        hidx = torch.empty(nh * inst.N, dtype=torch.int32).pin_memory().numpy()
-        hsl = torch.empty(nh * inst.N, dtype=torch.float32).pin_memory().numpy()
-        hs = E.Solver([inst], keep_ev=True, no_validate=True)
+        hs = E.Solver([inst], no_validate=True)
         hs.autotune()
 
         def host_step():
             hs.solve(hp["price"], hp["trans"], hp["cost"], hp["terminal"], hV1)
-            hs.bid_curves_packed(0, 1, inst.T + 1, hoff, hidx, hsl)
         for _ in range(args.warmup):
             host_step()
         times = []
@@ -350,11 +396,11 @@ def run_esdp(args, rank, world):
             host_step()
             times.append(time.perf_counter() - t0)
         h2d = sum(v.nbytes for v in hp.values())
-        d2h = hV1.nbytes + hoff.nbytes + 8 * int(hoff[-1])  # V_1, offsets, vertices + slopes
+        d2h = hV1.nbytes
         e2e = {"value": inst.evals / (sum(times) / len(times)), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": sum(times) / len(times) * 1e3,
-               "api": "host pointers: esdp_solve + esdp_bid_curves_packed, pinned buffers"}
+               "api": "host pointers: esdp_solve (inputs in, V_1 out), pinned buffers"}
         hs.close()
 
     extras = {}
@@ -366,18 +412,16 @@ def run_esdp(args, rank, world):
                 extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
 
     if rank == 0:
-        cpu = None if args.no_cpu else cpu_baseline_c2()
+        cpu = None if args.no_cpu else cpu_baseline_c3()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "evals_per_step": inst.evals, "l2": "flushed between steps (512 MB)",
-                       "parallelism": f"replicas x{world}", "launch": info},
-            "sweep_ms": t_sweep / args.steps * 1e3, "bid_curves_ms": t_hull / args.steps * 1e3,
+            "config": config, "launch": info,
+            "sweep_ms": t_sweep / args.steps * 1e3,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 4 * args.steps, "extra": extras,
+            "gpu_launches": 2 * args.steps, "extra": extras,
         }
         print(json.dumps(line), flush=True)
 
@@ -414,14 +458,23 @@ def bench_config1(torch, E, I, stream, flush, args, n_sm, f_max):
             "launch": info}
 
 
-def bench_config3(torch, E, I, stream, flush, args, n_sm, f_max):
-    """Large single asset: the persistent sweep alone (policy kept)."""
-    inst = I.config3()
+def bench_config2(torch, E, I, stream, flush, args, n_sm, f_max):
+    """The 5-minute two-mode asset (T=288, N=1001, K=20, A=201, switch cost):
+    the sweep (EV kept) and the convexified bid curves of every (t, m, k),
+    CUDA events per step, the sweep kernel alone from the library's own
+    events around its launch; L2 flushed between steps."""
+    inst = I.config2()
     cat = E.concat_inputs([inst])
     d = {k: torch.from_numpy(v).to("cuda") for k, v in cat.items()}
-    V1 = torch.empty(inst.N * inst.K, device="cuda")
-    s = E.Solver([inst], device_ptrs=True)
+    MNK = inst.n_modes * inst.N * inst.K
+    V1 = torch.empty(MNK, device="cuda")
+    nh = inst.T * inst.n_modes * inst.K
+    n_bp = torch.empty(nh, dtype=torch.int32, device="cuda")
+    idx = torch.empty(nh * inst.N, dtype=torch.int32, device="cuda")
+    slope = torch.empty(nh * inst.N, dtype=torch.float32, device="cuda")
+    s = E.Solver([inst], device_ptrs=True, keep_ev=True, time_sweep=True)
     s.autotune(stream=stream)
+    sweeps = []
 
     def step(evs):
         st = torch.cuda.current_stream()
@@ -430,14 +483,35 @@ def bench_config3(torch, E, I, stream, flush, args, n_sm, f_max):
         s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1, stream=st)
         if evs:
             evs[1].record(st)
-    n = max(3, min(args.steps, 5))
-    total, _ = time_steps(torch, step, n, 2, stream, flush)
-    ev_s = inst.evals * n / total
+        s.bid_curves(0, 1, inst.T + 1, n_bp, idx, slope, stream=st)
+        if evs:
+            evs[2].record(st)
+            sweeps.append(None)
+    n = max(5, min(args.steps, 20))
+    for _ in range(2):
+        step(None)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+    for i in range(n):
+        with torch.cuda.stream(stream):
+            flush()
+            step(ev[i])
+        sweeps[-1] = s.sweep_ms()
+    torch.cuda.synchronize()
+    assert s.status(stream=stream) == 0
+    t_solve = sum(e[0].elapsed_time(e[1]) for e in ev) / n
+    t_hull = sum(e[1].elapsed_time(e[2]) for e in ev) / n
+    t_sweep = sum(sweeps) / n
     peak = alu_peak_evals(n_sm, f_max)
     info = s.launch_info()
     s.close()
-    return {"evals_per_s": ev_s, "ms": total / n * 1e3, "frac_alu": ev_s / peak,
-            "launch": info, "steps": n}
+    return {"workload": "config2: T=288 N=1001 K=20 A=201 modes=2, sweep + bid curves of every "
+                        "(t,m,k)",
+            "step_ms": t_solve + t_hull, "solve_ms": t_solve, "sweep_kernel_ms": t_sweep,
+            "bid_curves_ms": t_hull, "evals_per_s": inst.evals / (t_solve + t_hull) * 1e3,
+            "sweep_evals_per_s": inst.evals / t_sweep * 1e3,
+            "frac_alu": inst.evals / t_sweep * 1e3 / peak,
+            "traffic": measured_traffic("traffic_config2.json"), "launch": info, "steps": n}
 
 
 def bench_config4(torch, E, I, stream, flush, args, n_sm, f_max):
@@ -553,9 +627,11 @@ TABLE3_PAPER_CPU_S = [3.98, 18.29, 98.12, 397.80, 1996.02, 9972.64]
 
 
 def bench_table3(torch, E, I, stream, flush, args, n_sm, f_max):
-    """Algorithm 1 on the Table III shapes (esdp_solve_iid, values only):
-    wall time of the blocking call (workspace allocation included), inputs
-    already on the device."""
+    """Algorithm 1 on the Table III shapes (esdp_solve_iid, values only,
+    inputs on the device): the device time of the sweep (CUDA events the
+    library records on its stream around the stage-probability sums and the
+    persistent launch, the workspace set-up outside them), median of 5
+    repeats after a warm-up, L2 flushed before each."""
     out = []
     for case in range(len(I.TABLE3_CASES)):
         prob = I.table3_problem(case)
@@ -564,14 +640,18 @@ def bench_table3(torch, E, I, stream, flush, args, n_sm, f_max):
         V0 = torch.empty(prob.S, device="cuda")
         P = len(E.iid_actions(prob))
         evals = prob.T * prob.S * P * prob.R
-        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)   # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi)
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
+        st = torch.cuda.current_stream()
+        E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi, stream=st)   # warm-up
+        ms = []
+        for _ in range(5):
+            flush()
+            E.solve_iid(prob, V0, device=True, lam_hat=lam, pi_hat=pi, stream=st)
+            ms.append(E.iid_last_sweep_ms())
+        ms.sort()
+        sec = ms[len(ms) // 2] / 1e3
         out.append({"case": prob.name, "T": prob.T, "S": prob.S, "P": P, "R": prob.R,
-                    "evals": evals, "seconds": sec, "evals_per_s": evals / sec,
+                    "evals": evals, "seconds": sec, "seconds_all": [m / 1e3 for m in ms],
+                    "evals_per_s": evals / sec,
                     "frac_alu": evals / sec / alu_peak_evals(n_sm, f_max),
                     "paper_gpu_s_l40s": TABLE3_PAPER_GPU_S[case],
                     "paper_cpu_s_xeon32": TABLE3_PAPER_CPU_S[case],
@@ -660,7 +740,8 @@ def bench_alu_probe(torch, E, I, stream, flush, args, n_sm, f_max):
     return out
 
 
-EXTRAS = {"config1": bench_config1, "config3": bench_config3, "config4": bench_config4, "config5": bench_config5,
+EXTRAS = {"config1": bench_config1, "config2": bench_config2, "config4": bench_config4,
+          "config5": bench_config5,
           "paper_table3": bench_table3, "paper_bids_clearing": bench_bids_clearing,
           "alu_probe": bench_alu_probe, "config2_bids_at": bench_bids_at}
 
@@ -739,8 +820,42 @@ def run_profile_case(name):
     print(json.dumps({"profile_case": name, "launch": s.launch_info()}))
 
 
+def run_phase_clocks():
+    """The sweep's per-stage phase cycles (clock64 of each CTA's first
+    thread, averaged over CTAs and stages) of an autotuned config3 and
+    config2 solve, from libesdp_phase.so: the same kernels with counters
+    between the phases, so the totals run a little above the plain build's."""
+    import torch
+    from paper_2511_15629_b300 import build as B
+    from paper_2511_15629_b300 import esdp as E
+    from paper_2511_15629_b300 import instances as I
+    E.load_library(B.build(phase_clocks=True))
+    out = {}
+    for name, inst in (("config3", I.config3()), ("config2", I.config2())):
+        d = {k: torch.from_numpy(v).to("cuda") for k, v in E.concat_inputs([inst]).items()}
+        V1 = torch.empty(inst.n_modes * inst.N * inst.K, device="cuda")
+        s = E.Solver([inst], device_ptrs=True, time_sweep=True)
+        s.autotune()
+        for _ in range(2):
+            s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+        torch.cuda.synchronize()
+        ph = s.phase_clocks()
+        ph["total"] = sum(ph.values())
+        out[name] = {"cycles_per_stage": {k: round(v) for k, v in ph.items()},
+                     "sweep_ms": s.sweep_ms(), "launch": s.launch_info(),
+                     "stages": inst.T, "evals_per_stage_per_cta":
+                     inst.n_modes * inst.N * inst.K * inst.A / s.launch_info()["grid"]}
+        s.close()
+    print(json.dumps({"phase_clocks": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.phase_clocks:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        run_phase_clocks()
+        return
     if args.profile_case:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

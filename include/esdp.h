@@ -66,6 +66,8 @@ extern "C" {
 #define ESDP_CHECK_ROWS 4u  /* reject transition rows whose sum is not 1 +- 1e-5 */
 #define ESDP_NO_VALIDATE 8u /* skip the host-side NaN / sign scan of inputs
                                (only meaningful with host pointers) */
+#define ESDP_TIME_SWEEP 16u /* record CUDA events around the persistent sweep
+                               launch of every esdp_solve (esdp_sweep_ms) */
 
 typedef struct esdp_ctx esdp_ctx;
 
@@ -84,8 +86,17 @@ typedef struct {
 } esdp_asset;
 
 /* Create a context for `n_assets` assets solved together (one persistent,
- * batched launch).  Validates the shapes, allocates the device workspace on
- * the current CUDA device and picks tile shapes (see esdp_autotune). */
+ * batched launch).  The asset description is the problem statement of
+ * Sec. II-B (SoC bound s_max and grid of eq. 12, efficiencies of eq. 2, the
+ * action band of eq. 13's integer interior); solving several assets in one
+ * launch has no counterpart in the paper.  Validates the shapes (ESDP_EINVAL
+ * with a message; on any failure after the context itself was allocated
+ * *out is a context that carries the message and must still be destroyed;
+ * *out is NULL when `out` or `assets` is NULL, n_assets < 1 or the context
+ * could not be allocated), allocates the device
+ * workspace on the current CUDA device (ESDP_ENOMEM) and picks tile shapes
+ * (see esdp_autotune).  The caller owns *out and frees it with
+ * esdp_destroy. */
 int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp_ctx** out);
 
 /* Backward induction over all assets (Algorithm 1, eq. 5-6).
@@ -97,8 +108,12 @@ int esdp_solve(esdp_ctx* ctx, const float* price, const float* trans, const floa
                const float* terminal, float* V1, void* stream);
 
 /* Policy of stage t (1..T) of `asset`: [n_modes][N][K] action indices as
- * int32 or int16 (policy_bytes).  ESDP_ESTATE when the context keeps no full
- * policy (policy_bytes == 0 or ckpt_every > 0) or before esdp_solve. */
+ * int32 or int16 (policy_bytes), the smallest maximiser of the Bellman step
+ * (eq. 5; Algorithm 1 keeps only the maximum, the argmax is this library's
+ * addition).  `out` is a host or device pointer as the context's flags say;
+ * the caller owns it.  ESDP_EINVAL for a bad asset or stage index,
+ * ESDP_ESTATE when the context keeps no full policy (policy_bytes == 0 or
+ * ckpt_every > 0) or before esdp_solve. */
 int esdp_policy(esdp_ctx* ctx, int32_t asset, int32_t t, void* out, void* stream);
 
 /* EV_t (1..T) of `asset`: [n_modes][N][K] float (needs ESDP_KEEP_EV). */
@@ -187,6 +202,9 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
 
 /* Re-time the candidate tile shapes / actions-per-warp on the device and
  * keep the fastest (results are cached per shape class for the process).
+ * The paper has no counterpart (its sweep is one library broadcast per
+ * stage); the shapes only change how the Bellman step of eq. 5 is tiled,
+ * not its result up to float32 rounding of the EV contraction.
  * With the environment variable ESDP_SHAPE="R,block" (rows per thread
  * 4/6/8/10/12, threads per block) that shape is used without timing;
  * ESDP_EINVAL if it cannot be built for the context's assets.  The results
@@ -194,6 +212,26 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
  * context's workspace): policy, EV, bid curves and esdp_grad answer
  * ESDP_ESTATE until the next solve. */
 int esdp_autotune(esdp_ctx* ctx, void* stream);
+
+/* Device time in milliseconds of the persistent sweep kernel of the last
+ * esdp_solve (CUDA events recorded on its stream right before and after the
+ * launch, so the input copies, the row-sum preparation and the EV level
+ * restore are outside it); waits for that launch to finish.  A measurement
+ * aid with no counterpart in the paper.  ESDP_ESTATE when the context was
+ * made without ESDP_TIME_SWEEP or has not solved yet. */
+int esdp_sweep_ms(esdp_ctx* ctx, float* ms);
+
+/* Per-stage cycle counts of the phases of the last esdp_solve's sweep,
+ * averaged over its CTAs and stages (clock64 of each CTA's first thread):
+ * 0 inputs of the stage, 1 neighbour wait (other warps write the previous
+ * stage's outputs meanwhile), 2 EV halo copy and stage level, 3 banded
+ * max-plus loop, 4 part merge and argmax recovery, 5 EV contraction,
+ * 6 release, 7 next-stage loads and output bookkeeping.  Only a library
+ * built with -DESDP_PHASE_CLOCKS counts them (the package's build script
+ * makes it as libesdp_phase.so); the regular library returns ESDP_ESTATE.
+ * cycles [n_phases >= 8] out.  A measurement aid with no counterpart in the
+ * paper. */
+int esdp_phase_clocks(esdp_ctx* ctx, double* cycles, int32_t n_phases);
 
 /* Device status word of the last launch: 0, or the ESDP_E* code a kernel
  * reported.  Synchronises `stream`. */
@@ -286,8 +324,8 @@ int esdp_iid_clear(const esdp_iid_problem* problem, const float* V_all, const fl
  * plug-in running inside an application that owns the device memory pool
  * through its own caching allocator, a process under a hard device-memory
  * quota, or code on a latency-critical path where an allocation could
- * stall.  It runs the same persistent sweep as esdp_solve (eq. 5-6,
- * Algorithm 1) but needs no context and allocates nothing: its workspace
+ * stall.  It runs the same persistent sweep as esdp_solve but needs no
+ * context and allocates nothing: its workspace
  * (EV halo buffers, neighbour flags, status word, stage levels, launch plan)
  * is one file-scope device array of ESDP_NOALLOC_SCRATCH_BYTES that every
  * GPU loading this library reserves until the process exits.
@@ -304,9 +342,12 @@ int esdp_iid_clear(const esdp_iid_problem* problem, const float* V_all, const fl
  * plus 2*T*K doubles of per-stage data (N*K up to roughly 1.9 million for one
  * mode and T = 288), and at most 2048 tiles; larger assets are rejected with
  * ESDP_EINVAL and a message that states the bytes needed.
- * The first call on a device looks up the workspace address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one
+ * Every call looks up the workspace address (cudaGetSymbolAddress) with
+ * the caller's device current, so a new context or a device reset is
+ * picked up; the first call on a device also loads the library's device
+ * code there, so make that first call before any stream capture.  The
+ * bounded device waits give up after ESDP_TIMEOUT_MS milliseconds (default
+ * 5000) with ESDP_ETIMEOUT, as in esdp_solve.  Every call on a device shares the one
  * workspace: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller. */
 #define ESDP_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -325,7 +366,19 @@ int esdp_solve_noalloc(const esdp_asset* asset, const float* price, const float*
 int esdp_alu_probe(int32_t kind, int32_t iters, double* instr_per_clk, double* elem_per_clk,
                    void* stream);
 
+/* Device time in milliseconds (CUDA events on the call's stream) of the
+ * sweep of the last successful esdp_solve_iid made by this host thread: the
+ * stage-probability sums and the persistent Algorithm 1 launch, without the
+ * workspace allocation and the copies around them; a negative value before
+ * any such call.  A measurement aid with no counterpart in the paper. */
+double esdp_iid_last_sweep_ms(void);
+
+/* Free a context and its device workspace (no counterpart in the paper).
+ * NULL is accepted.  The caller must not use the context afterwards, and no
+ * work queued with it may still be running on the device. */
 void esdp_destroy(esdp_ctx* ctx);
+/* Message of the context's last failed call ("" if none; a static message
+ * when ctx is NULL).  Owned by the context, valid until its next call. */
 const char* esdp_last_error(const esdp_ctx* ctx);
 int esdp_version(void);
 

@@ -7,6 +7,9 @@ shares no code with the CUDA library.
 Pieces:
   * ``solve``      -- ctypes wrapper of the C backward induction (eq. 4-6 with
                       a Markov price chain, Alg. 1 in plain loops);
+  * ``action_value`` -- the FP64 value of one given action in one state
+                      (payoff + EV at the shifted SoC, eq. 5), to check that
+                      a decision taken elsewhere is a maximiser;
   * ``hull``       -- monotone-chain upper envelope (eq. 10-11);
   * ``markov_bids_at`` -- price-quantity bids at one SoC state from that
                       envelope, re-convexified over grid power (eq. 8-11);
@@ -126,6 +129,33 @@ def solve(inst, *, keep_V: bool = False, keep_EV: bool = False, keep_policy: boo
     if rc != 0:
         raise ValueError(f"orc_solve failed ({rc})")
     return out
+
+
+def action_value(inst, t: int, EV_t: np.ndarray, m, s, k, a, price=None) -> np.ndarray:
+    """FP64 value of taking action a in state (m, s, k) at stage t (eq. 5):
+    the payoff price[t,k] e_a - cost[a] (- switch cost when a discharge
+    leaves mode 1) plus EV_t[m'][s + d][k] at the shifted SoC, d = a - D_dis,
+    m' the mode after the action; -inf where s + d leaves the grid (eq. 4).
+    EV_t: [M, N, K] (any float dtype, promoted to float64); m, s, k, a:
+    integer arrays of one shape (broadcast).  The same double operations, in
+    the same order, as the C oracle's Bellman step, so that at the oracle's
+    own policy it reproduces V_t bit for bit."""
+    m, s, k, a = (np.asarray(x, dtype=np.int64) for x in np.broadcast_arrays(m, s, k, a))
+    d = a - inst.D_dis
+    delta = inst.s_max / float(inst.N - 1)
+    e = np.where(d < 0, (-d.astype(np.float64) * delta) * inst.eta_d,
+                 np.where(d > 0, (-d.astype(np.float64) * delta) / inst.eta_c, 0.0))
+    lam = np.asarray(inst.price if price is None else price, np.float64)[t - 1, k]
+    r = lam * e - np.asarray(inst.cost, np.float64)[a]
+    if inst.n_modes == 2:
+        r = np.where((m == 1) & (d < 0), r - inst.switch_cost, r)
+        m2 = np.where(d < 0, 0, np.where(d > 0, 1, m))
+    else:
+        m2 = np.zeros_like(m)
+    s2 = s + d
+    ok = (s2 >= 0) & (s2 <= inst.N - 1)
+    ev = np.asarray(EV_t, np.float64)[m2, np.clip(s2, 0, inst.N - 1), k]
+    return np.where(ok, r + ev, -np.inf)
 
 
 def objective(inst, V1: np.ndarray) -> float:

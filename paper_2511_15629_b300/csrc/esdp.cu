@@ -105,6 +105,12 @@ struct esdp_ctx {
   std::vector<Plan> solo;         // per-asset plans for the gradient recompute
   std::string err;
   unsigned long long timeout_ns = 5ull * 1000 * 1000 * 1000;
+  // ESDP_TIME_SWEEP: events recorded around the sweep launch of esdp_solve
+  cudaEvent_t ev_sweep[2] = {nullptr, nullptr};
+  bool sweep_recorded = false;
+  // per-CTA phase cycle counters of the last main sweep (ESDP_PHASE_CLOCKS builds)
+  unsigned long long* d_phase = nullptr;
+  int phase_grid = 0;
 };
 
 namespace {
@@ -455,7 +461,27 @@ int run_plan(esdp_ctx* c, Plan* p, const float* price, const float* trans, const
     CK(launch_rowsums(p->d_assets, (int)p->adev.size(), p->max_rows, trans, st), "row sums");
     for (size_t j = 0; j < p->adev.size(); ++j) c->prep_tc[p->asset_ids[j]] = p->adev[j].tc;
   }
+#ifdef ESDP_PHASE_CLOCKS
+  if (p == &c->main) {
+    if (c->phase_grid < p->shape.grid) {
+      cudaFree(c->d_phase);
+      c->d_phase = nullptr;
+      c->phase_grid = 0;
+      CK(cudaMalloc(&c->d_phase, (size_t)p->shape.grid * (kPhases + 1) * 8), "phase counters");
+      c->phase_grid = p->shape.grid;
+    }
+    CK(cudaMemsetAsync(c->d_phase, 0, (size_t)c->phase_grid * (kPhases + 1) * 8, st),
+       "phase counters");
+    sp.phase_clk = c->d_phase;
+  }
+#endif
+  const bool timed = p == &c->main && c->ev_sweep[0] != nullptr;
+  if (timed) CK(cudaEventRecord(c->ev_sweep[0], st), "sweep timing event");
   CK(launch_sweep(p->shape, sp, st), "sweep launch");
+  if (timed) {
+    CK(cudaEventRecord(c->ev_sweep[1], st), "sweep timing event");
+    c->sweep_recorded = true;
+  }
   return ESDP_OK;
 }
 
@@ -597,6 +623,10 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
   }
   if (getenv("ESDP_FAIL_ALLOC")) return fail(c, ESDP_ENOMEM, "allocation failure injected");
   CK(cudaGetDevice(&c->device), "cudaGetDevice");
+  if (flags & ESDP_TIME_SWEEP) {
+    CK(cudaEventCreate(&c->ev_sweep[0]), "sweep timing event");
+    CK(cudaEventCreate(&c->ev_sweep[1]), "sweep timing event");
+  }
   int coop = 0;
   CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device), "device attribute");
   if (!coop) return fail(c, ESDP_ECUDA, "device has no cooperative launch support");
@@ -701,9 +731,42 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
   return ESDP_OK;
 }
 
+int esdp_sweep_ms(esdp_ctx* c, float* ms) {
+  if (!c || !ms) return ESDP_EINVAL;
+  if (!c->ev_sweep[0]) return fail(c, ESDP_ESTATE, "context made without ESDP_TIME_SWEEP");
+  if (!c->sweep_recorded) return fail(c, ESDP_ESTATE, "no sweep launched yet");
+  CK(cudaEventSynchronize(c->ev_sweep[1]), "sweep timing");
+  CK(cudaEventElapsedTime(ms, c->ev_sweep[0], c->ev_sweep[1]), "sweep timing");
+  return ESDP_OK;
+}
+
+int esdp_phase_clocks(esdp_ctx* c, double* cycles, int32_t n_phases) {
+  if (!c || !cycles || n_phases < kPhases) return ESDP_EINVAL;
+#ifdef ESDP_PHASE_CLOCKS
+  if (!c->d_phase || !c->solved) return fail(c, ESDP_ESTATE, "no instrumented sweep has run");
+  std::vector<unsigned long long> h((size_t)c->phase_grid * (kPhases + 1));
+  CK(cudaDeviceSynchronize(), "phase counters");
+  CK(cudaMemcpy(h.data(), c->d_phase, h.size() * 8, cudaMemcpyDeviceToHost), "phase counters");
+  double stages = 0;
+  std::vector<double> sum(kPhases, 0.0);
+  for (int g = 0; g < c->phase_grid; ++g) {
+    stages += (double)h[(size_t)g * (kPhases + 1) + kPhases];
+    for (int i = 0; i < kPhases; ++i) sum[i] += (double)h[(size_t)g * (kPhases + 1) + i];
+  }
+  for (int i = 0; i < kPhases; ++i) cycles[i] = stages > 0 ? sum[i] / stages : 0.0;
+  return ESDP_OK;
+#else
+  (void)cycles;
+  return fail(c, ESDP_ESTATE, "library built without ESDP_PHASE_CLOCKS");
+#endif
+}
+
 void esdp_destroy(esdp_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  cudaFree(c->d_phase);
+  for (cudaEvent_t& e : c->ev_sweep)
+    if (e) cudaEventDestroy(e);
   free_plan(&c->main);
   for (Plan& p : c->solo) free_plan(&p);
   for (void* p : c->allocs) cudaFree(p);

@@ -131,7 +131,14 @@ struct SweepParams {
   int sm_E, sm_R, sm_C, sm_V, sm_P, sm_X;
   int sm_A, sm_A2;           // tcgen05 A operand (V' split into tf32 hi and lo parts)
   int tmem_cols;             // tensor-memory columns of the EV accumulator (0: none)
+  // per-CTA phase cycle sums [grid][kPhases + 1] (the last slot counts the
+  // stages), written only by a library built with ESDP_PHASE_CLOCKS
+  unsigned long long* phase_clk;
 };
+
+// Phases of one stage of one work item, as the per-phase clock counters of
+// an ESDP_PHASE_CLOCKS build split it (cycles of thread 0 of the CTA).
+constexpr int kPhases = 8;
 
 // Row strides of the V' tile and of the transposed transition matrix in
 // shared memory (and of the prepared transposed copy in global memory),

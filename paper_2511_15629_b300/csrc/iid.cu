@@ -518,6 +518,9 @@ std::vector<double> action_grid(const esdp_iid_problem& q) {
   return p;
 }
 
+// Device time of the last successful esdp_solve_iid of this host thread.
+thread_local double g_iid_sweep_ms = -1.0;
+
 }  // namespace
 }  // namespace esdp
 
@@ -697,10 +700,16 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
   ip.v_all = V_all ? (dev ? V_all : (float*)d_vall) : nullptr;
   ip.cta_first = (const int*)d_cta;
   ip.timeout_ns = 5ull * 1000 * 1000 * 1000;
+  // device time of the sweep (events on the call's stream, the workspace set
+  // up before them), kept per host thread for esdp_iid_last_sweep_ms
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  const bool timed = cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess &&
+                     cudaEventRecord(ev0, st) == cudaSuccess;
   iid_rho_kernel<<<(T + 127) / 128, 128, 0, st>>>(ip.pi, (double*)d_rho, T, R);
   void* args[] = {&ip};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kIidBlock), args,
                                               smem, st);
+  const bool timed_end = timed && e == cudaSuccess && cudaEventRecord(ev1, st) == cudaSuccess;
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && !dev) {
@@ -711,6 +720,10 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
       e = cudaMemcpyAsync(V_all, d_vall, (size_t)(T + 1) * S * 4, cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = -1.f;
+  if (e == cudaSuccess && timed_end && cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) ms = -1.f;
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   cleanup();
   if (e != cudaSuccess) {
     std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
@@ -720,8 +733,11 @@ extern "C" int esdp_solve_iid(const esdp_iid_problem* q, const float* lam_hat, c
     std::snprintf(buf, sizeof(buf), "device reported status %d", status);
     return msg(err, err_len, status, buf);
   }
+  g_iid_sweep_ms = ms;
   return ESDP_OK;
 }
+
+extern "C" double esdp_iid_last_sweep_ms(void) { return g_iid_sweep_ms; }
 
 namespace {
 

@@ -14,8 +14,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/esdp.h"
 #include "esdp_internal.h"
@@ -25,15 +25,11 @@ namespace {
 
 constexpr size_t kNoAllocBytes = size_t(16) << 20;  // ESDP_NOALLOC_SCRATCH_BYTES
 constexpr int kNoAllocMaxItems = 2048;
-constexpr int kMaxDevices = 64;
 constexpr size_t kSmemLimit = 227 * 1024;
 
 // The workspace.  Every call on a device reuses it; its contents persist
 // between calls, so everything that must start at zero is cleared per call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
 
 // Grid energy of each action (eq. 2), in double then rounded once.
 __global__ void energy_kernel(float* e, int A, int D_dis, double delta, double eta_c,
@@ -78,29 +74,34 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   if (a.T < 1 || a.N < 2 || a.K < 1 || a.K > 128 || a.A < 1 || a.D_dis < 0 || a.D_chg < 0 ||
       a.D_dis + a.D_chg + 1 != a.A || a.D_dis > a.N - 1 || a.D_chg > a.N - 1 ||
       (a.n_modes != 1 && a.n_modes != 2) || !(a.eta_c > 0 && a.eta_c <= 1) ||
-      !(a.eta_d > 0 && a.eta_d <= 1) || !(a.s_max > 0) || !std::isfinite(a.switch_cost) ||
-      (policy && a.policy_bytes != 2 && a.policy_bytes != 4))
+      !(a.eta_d > 0 && a.eta_d <= 1) || !(a.s_max > 0) || !std::isfinite(a.s_max) ||
+      !std::isfinite(a.switch_cost) || (policy && a.policy_bytes != 2 && a.policy_bytes != 4))
     return msg(err, err_len, ESDP_EINVAL, "invalid asset description");
+  if (policy && a.policy_bytes == 2 && a.A > 32767)
+    return msg(err, err_len, ESDP_EINVAL, "int16 policies need A <= 32767");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+  if (cudaGetDevice(&dev) != cudaSuccess)
     return msg(err, err_len, ESDP_ECUDA, "no current CUDA device");
-  // one-time set-up per device: the device address of the workspace
+  // the device address of the workspace in the current context, looked up
+  // on every call: a cached address would go stale after a device reset or
+  // under another context of the same device
   void* base = nullptr;
   {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the workspace failed: %s",
-                 cudaGetErrorString(e));
-        return msg(err, err_len, ESDP_ECUDA, buf);
-      }
-      g_addr[dev] = p;
+    const cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess || !base) {
+      snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the workspace failed: %s",
+               cudaGetErrorString(e));
+      return msg(err, err_len, ESDP_ECUDA, buf);
     }
-    base = g_addr[dev];
   }
+  // bounded device waits: the same limit and test hook as esdp_solve
+  unsigned long long timeout_ns = 5ull * 1000 * 1000 * 1000;
+  if (const char* env = std::getenv("ESDP_TIMEOUT_MS")) {
+    const long long ms = std::atoll(env);
+    if (ms > 0) timeout_ns = (unsigned long long)ms * 1000000ull;
+  }
+  const int wait_extra = std::getenv("ESDP_INJECT_STALL") ? 1000000 : 0;
   int n_sm = 0;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return msg(err, err_len, ESDP_ECUDA, "device attribute query failed");
@@ -232,8 +233,8 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   sp.n_steps = a.T;
   sp.flags = reinterpret_cast<int*>(S + o_flags);
   sp.status = reinterpret_cast<int*>(S + o_status);
-  sp.timeout_ns = 5ull * 1000 * 1000 * 1000;
-  sp.wait_extra = 0;
+  sp.timeout_ns = timeout_ns;
+  sp.wait_extra = wait_extra;
   sp.item_c = reinterpret_cast<double*>(S + o_itemc);
   sp.sm_E = L.E;
   sp.sm_R = L.Rt;

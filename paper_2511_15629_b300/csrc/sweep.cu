@@ -37,6 +37,31 @@
 namespace esdp {
 namespace {
 
+// Per-phase cycle counters of thread 0 (a build with -DESDP_PHASE_CLOCKS
+// only; otherwise these compile to nothing).  PHASE_MARK(i) adds the cycles
+// since the previous mark to phase i.
+#ifdef ESDP_PHASE_CLOCKS
+struct PhaseClock {
+  unsigned long long last = 0, acc[kPhases + 1] = {};
+};
+#define PHASE_DECL PhaseClock& pc,
+#define PHASE_ARG pc,
+#define PHASE_MARK(i)                                    \
+  do {                                                   \
+    if (threadIdx.x == 0) {                              \
+      const unsigned long long now_ = clock64();         \
+      pc.acc[(i)] += now_ - pc.last;                     \
+      pc.last = now_;                                    \
+    }                                                    \
+  } while (0)
+#else
+#define PHASE_DECL
+#define PHASE_ARG
+#define PHASE_MARK(i) \
+  do {                \
+  } while (0)
+#endif
+
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -671,10 +696,10 @@ struct Deferred {
 
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
-__device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkItem& w, int it,
-                           int g, const Smem& sm, uint32_t& parity, uint32_t& parity_p,
-                           uint32_t& parity_m, bool p_pref, const StageScalars& pre,
-                           const Deferred& def) {
+__device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
+                           const WorkItem& w, int it, int g, const Smem& sm, uint32_t& parity,
+                           uint32_t& parity_p, uint32_t& parity_m, bool p_pref,
+                           const StageScalars& pre, const Deferred& def) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -688,6 +713,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   const bool p_bulk = p_pref || (t > as.t_lo && load_trans_async(p, as, t - 1, sm.Ps, sm.barP));
   double c_next = pre.c;
   if (!pre.valid) stage_scalars(p, as, t, it, sm, c_next, false);
+  PHASE_MARK(0);
 
   // 1. neighbours; meanwhile the warps that do not poll write the previous
   //    stage's outputs (its V' tile and indices are still in place)
@@ -696,7 +722,13 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     const int first = (n_wait + 31) & ~31;
     item_outputs(p, as, def.w, def.t, sm, first < (int)blockDim.x ? first : 0);
   }
-  if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) return false;
+  if (!wait_neighbours(p, as, w, g + 1 + p.wait_extra, t, sm.abort, sm.ref)) {
+    // abandoning the launch: first let this CTA's own copy of P_{t-1} land
+    // (bounded), so that no bulk copy into its shared memory is in flight
+    if (p_bulk && tid == 0) mbar_wait_bounded(sm.barP, parity_p, p);
+    return false;
+  }
+  PHASE_MARK(1);
 
   // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
   const float* ev_t = ev_ptr(as, t);
@@ -761,6 +793,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
   }
   __syncthreads();
   if (*(volatile int*)sm.abort) return false;
+  PHASE_MARK(2);
 
   // 3. banded max-plus.  A cell is (pair of price states, block of R rows,
   //    mode); its chunks of R actions are split into G = parts contiguous
@@ -818,6 +851,7 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
       }
     }
     for (; c < c_hi; ++c) chunk(c);
+    PHASE_MARK(3);
     // merge the parts of each cell: the larger value, on equal values the
     // earlier chunk (the parts hold increasing action ranges)
     for (int d = L; d < 32; d <<= 1) {
@@ -894,9 +928,11 @@ __device__ bool item_stage(const SweepParams& p, const AssetDev& as, const WorkI
     }
   }
   __syncthreads();
+  PHASE_MARK(4);
 
   // 5. EV'_{t-1} of the item's own rows
   if (t > as.t_lo) expectation(p, as, w, t - 1, sm, parity_m);
+  PHASE_MARK(5);
   return true;
 }
 
@@ -973,6 +1009,9 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
 template <int R>
 __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, AssetDev& s_as) {
   const int i0 = p.cta_items[blockIdx.x], i1 = p.cta_items[blockIdx.x + 1];
+#ifdef ESDP_PHASE_CLOCKS
+  PhaseClock pc;
+#endif
   uint32_t parity = 0, parity_p = 0, parity_m = 0;
   // the work item's asset descriptor lives in shared memory: the loops that
   // store to global memory then need not reload its fields
@@ -1026,6 +1065,9 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
   int nx_idx = -1;
   WorkItem nx{};
   Deferred def;
+#ifdef ESDP_PHASE_CLOCKS
+  if (threadIdx.x == 0) pc.last = clock64();
+#endif
   for (int g = 0; g < p.n_steps; ++g) {
     for (int it = i0; it < i1; ++it) {
       const WorkItem w = it == nx_idx ? nx : p.items[it];
@@ -1043,9 +1085,12 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre, def)) return;
+      if (!item_stage<R>(PHASE_ARG p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre,
+                         def))
+        return;
       def.it = -1;
       publish(p.flags + as.flag_base + w.tile, g + 2);
+      PHASE_MARK(6);
       // start the next stage's loads now when that stage is of the same
       // asset: their latency then overlaps the output stores and the wait
       {
@@ -1069,9 +1114,17 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
           item_outputs(p, as, w, as.t_hi - g, sm, 0);
         }
       }
+      PHASE_MARK(7);
+#ifdef ESDP_PHASE_CLOCKS
+      if (threadIdx.x == 0) pc.acc[kPhases] += 1;  // stages counted
+#endif
     }
   }
   if (def.it >= 0) item_outputs(p, s_as, def.w, def.t, sm, 0);
+#ifdef ESDP_PHASE_CLOCKS
+  if (threadIdx.x == 0 && p.phase_clk)
+    for (int i = 0; i <= kPhases; ++i) p.phase_clk[(size_t)blockIdx.x * (kPhases + 1) + i] = pc.acc[i];
+#endif
 }
 
 template <int R>

@@ -20,6 +20,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libesdp.so")
+# measurement build of the same sources (per-phase sweep clock counters)
+LIB_PHASE_PATH = os.path.join(_HERE, "libesdp_phase.so")
 
 ESDP_OK = 0
 ESDP_EINVAL = -1
@@ -33,12 +35,14 @@ ESDP_DEVICE_PTRS = 1
 ESDP_KEEP_EV = 2
 ESDP_CHECK_ROWS = 4
 ESDP_NO_VALIDATE = 8
+ESDP_TIME_SWEEP = 16
 
 EXPORTS = ["esdp_create", "esdp_solve", "esdp_policy", "esdp_expected_value", "esdp_bid_curves",
            "esdp_bids_at", "esdp_bid_curves_packed",
            "esdp_objective", "esdp_grad", "esdp_iid_actions", "esdp_solve_iid", "esdp_iid_bids",
-           "esdp_iid_clear", "esdp_autotune", "esdp_alu_probe",
-           "esdp_status", "esdp_launch_info", "esdp_destroy", "esdp_last_error", "esdp_version"]
+           "esdp_iid_clear", "esdp_iid_last_sweep_ms", "esdp_autotune", "esdp_alu_probe",
+           "esdp_status", "esdp_sweep_ms", "esdp_phase_clocks", "esdp_launch_info", "esdp_destroy", "esdp_last_error",
+           "esdp_version"]
 
 
 class EsdpError(RuntimeError):
@@ -59,15 +63,20 @@ class Asset(ctypes.Structure):
 _lib = None
 
 
-def load_library():
-    """Load libesdp.so (raises if it has not been built)."""
+def load_library(path: Optional[str] = None):
+    """Load libesdp.so, or the library at `path` (the phase-clock build),
+    once per process; raises if it has not been built."""
     global _lib
     if _lib is not None:
+        if path is not None and getattr(_lib, "_esdp_path", LIB_PATH) != path:
+            raise RuntimeError(f"{_lib._esdp_path} is already loaded")
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
                            "`python -m paper_2511_15629_b300.build`")
-    lib = ctypes.CDLL(LIB_PATH)
+    lib = ctypes.CDLL(path)
+    lib._esdp_path = path
     vp = ctypes.c_void_p
     i32 = ctypes.c_int32
     lib.esdp_create.argtypes = [ctypes.POINTER(Asset), i32, ctypes.c_uint32, ctypes.POINTER(vp)]
@@ -81,6 +90,8 @@ def load_library():
     lib.esdp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.esdp_autotune.argtypes = [vp, vp]
     lib.esdp_status.argtypes = [vp, vp]
+    lib.esdp_sweep_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.esdp_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     lib.esdp_launch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 7
     lib.esdp_destroy.argtypes = [vp]
     lib.esdp_destroy.restype = None
@@ -89,9 +100,11 @@ def load_library():
     lib.esdp_version.argtypes = []
     lib.esdp_alu_probe.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.esdp_iid_last_sweep_ms.argtypes = []
     for name in EXPORTS:
         if name not in ("esdp_destroy", "esdp_last_error"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.esdp_iid_last_sweep_ms.restype = ctypes.c_double
     _lib = lib
     return lib
 
@@ -146,12 +159,13 @@ class Solver:
     """One esdp context over a list of assets (instances)."""
 
     def __init__(self, instances: Sequence, *, device_ptrs: bool = False, keep_ev: bool = False,
-                 check_rows: bool = False, no_validate: bool = False):
+                 check_rows: bool = False, no_validate: bool = False, time_sweep: bool = False):
         self._lib = load_library()
         self.instances = list(instances)
         self.device = device_ptrs
         flags = ((ESDP_DEVICE_PTRS if device_ptrs else 0) | (ESDP_KEEP_EV if keep_ev else 0)
-                 | (ESDP_CHECK_ROWS if check_rows else 0) | (ESDP_NO_VALIDATE if no_validate else 0))
+                 | (ESDP_CHECK_ROWS if check_rows else 0) | (ESDP_NO_VALIDATE if no_validate else 0)
+                 | (ESDP_TIME_SWEEP if time_sweep else 0))
         arr = (Asset * len(self.instances))(*[asset_from_instance(i) for i in self.instances])
         self._ctx = ctypes.c_void_p()
         rc = self._lib.esdp_create(arr, len(self.instances), flags, ctypes.byref(self._ctx))
@@ -348,6 +362,23 @@ class Solver:
     def status(self, stream=None) -> int:
         return int(self._lib.esdp_status(self._ctx, _stream(stream)))
 
+    PHASES = ("inputs", "neighbour wait", "EV halo copy + level", "max-plus loop",
+              "merge + argmax recovery", "EV contraction", "release", "next-stage issue")
+
+    def phase_clocks(self) -> dict:
+        """Per-stage cycles of each sweep phase of the last solve (needs the
+        library built with phase clocks: load_library(LIB_PHASE_PATH))."""
+        out = (ctypes.c_double * 8)()
+        self._check(self._lib.esdp_phase_clocks(self._ctx, out, 8))
+        return {name: float(v) for name, v in zip(self.PHASES, out)}
+
+    def sweep_ms(self) -> float:
+        """Device time (ms) of the last solve's sweep kernel (needs
+        time_sweep=True); waits for that launch."""
+        ms = ctypes.c_float()
+        self._check(self._lib.esdp_sweep_ms(self._ctx, ctypes.byref(ms)))
+        return float(ms.value)
+
     EV_PATHS = {0: "simt", 1: "tcgen05", 2: "mma.sync"}
 
     def launch_info(self) -> dict:
@@ -426,6 +457,12 @@ def solve_iid(prob, V0=None, policy=None, *, device=False, lam_hat=None, pi_hat=
     if keep_values and not device:
         out += (V_all,)
     return out if len(out) > 1 else V0
+
+
+def iid_last_sweep_ms() -> float:
+    """Device time (ms, CUDA events) of the sweep of this thread's last
+    successful solve_iid, without its workspace set-up; negative before any."""
+    return float(load_library().esdp_iid_last_sweep_ms())
 
 
 def iid_bids(prob, V_all, t0: int, t1: int, stream=None):

@@ -433,6 +433,36 @@ def test_tie_rule_smallest_action():
         assert np.all(r["gap"][:, 0, s, :] == 0.0)
 
 
+@pytest.mark.parametrize("modes", [1, 2])
+def test_action_value_reproduces_bellman_step(modes):
+    """action_value (the value of one given action) against the C oracle's
+    Bellman step on the same EV: at the oracle's policy it equals V_t bit for
+    bit, no action exceeds V_t, the best other action sits exactly `gap`
+    below, and infeasible shifts are -inf (a dropped payoff term, a wrong
+    sign of the switch cost or a wrong next mode breaks one of these)."""
+    inst = I.random_instance(36 + modes, 5, 23, 3, 4, 6, modes, neg_prob=0.3, cost="nonconvex",
+                             switch_cost=2.5, eta=(0.87, 0.93))
+    r = O.solve(inst, keep_V=True, keep_EV=True)
+    M, N, K, A = inst.n_modes, inst.N, inst.K, inst.A
+    m, s, k, a = np.meshgrid(np.arange(M), np.arange(N), np.arange(K), np.arange(A),
+                             indexing="ij")
+    for t in range(1, inst.T + 1):
+        q = O.action_value(inst, t, r["EV"][t - 1], m, s, k, a)
+        V = r["V"][t - 1]
+        pol = r["policy"][t - 1]
+        best = np.take_along_axis(q, pol[..., None], axis=3)[..., 0]
+        np.testing.assert_array_equal(best, V)
+        assert np.all(q <= V[..., None])
+        np.testing.assert_array_equal(q.max(axis=3), V)
+        others = q.copy()
+        np.put_along_axis(others, pol[..., None], -np.inf, axis=3)
+        second = others.max(axis=3)
+        fin = np.isfinite(second)
+        np.testing.assert_array_equal((V - second)[fin], r["gap"][t - 1][fin])
+        shift = s + (a - inst.D_dis)
+        assert np.all(np.isneginf(q[(shift < 0) | (shift > N - 1)]))
+
+
 # ------------------------------------------------------------- Monte Carlo
 
 @pytest.mark.parametrize("which", ["config1", "modes"])

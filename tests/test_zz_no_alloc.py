@@ -82,6 +82,58 @@ def test_noalloc_mma_path(monkeypatch, K):
     s.close()
 
 
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which loads the library's device code, and with
+    it the fixed workspace, on this device), further calls change neither
+    the device's free memory nor the caching allocator's reserved or
+    allocated bytes: the entry point allocates nothing."""
+    import torch
+    inst = I.random_instance(93, 7, 300, 5, 12, 10, 2, neg_prob=0.3)
+    d = _inputs(inst)
+    MNK = inst.n_modes * inst.N * inst.K
+    V1 = torch.empty(MNK, device="cuda")
+    pol = torch.empty(inst.T * MNK, dtype=torch.int32, device="cuda")
+    E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1, pol)
+    first = V1.clone()
+    torch.cuda.synchronize()
+    before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved(),
+              torch.cuda.memory_allocated())
+    for _ in range(3):
+        E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1, pol)
+    torch.cuda.synchronize()
+    after = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved(),
+             torch.cuda.memory_allocated())
+    assert after == before, f"device memory (free, reserved, allocated) {before} -> {after}"
+    assert torch.equal(V1, first)
+
+
+def test_noalloc_bounded_wait_times_out(monkeypatch):
+    """The allocation-free entry point's device waits are bounded like the
+    context's: with every wait made to wait for a flag value nothing
+    publishes (the ESDP_INJECT_STALL test hook) and a 300 ms limit, the call
+    returns ESDP_ETIMEOUT, and the next call on the same workspace is
+    correct again (the flags and the status word are cleared per call)."""
+    import torch
+    inst = I.random_instance(94, 5, 200, 4, 9, 9, 1, neg_prob=0.2)
+    d = _inputs(inst)
+    MNK = inst.n_modes * inst.N * inst.K
+    ref = torch.empty(MNK, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], ref)
+    torch.cuda.synchronize()
+    s.close()
+    V1 = torch.empty(MNK, device="cuda")
+    monkeypatch.setenv("ESDP_TIMEOUT_MS", "300")
+    monkeypatch.setenv("ESDP_INJECT_STALL", "1")
+    with pytest.raises(E.EsdpError) as ei:
+        E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    assert ei.value.code == E.ESDP_ETIMEOUT
+    monkeypatch.delenv("ESDP_INJECT_STALL")
+    E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1)
+    err = float((V1 - ref).abs().max()) / float(ref.abs().max())
+    assert err <= VTOL
+
+
 def test_noalloc_rejects_assets_beyond_the_workspace():
     import torch
     inst = I.random_instance(91, 2, 40000, 64, 3, 3, 1)
