@@ -206,7 +206,7 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
  * stage); the shapes only change how the Bellman step of eq. 5 is tiled,
  * not its result up to float32 rounding of the EV contraction.
  * With the environment variable ESDP_SHAPE="R,block" (rows per thread
- * 4/6/8/10/12, threads per block) that shape is used without timing;
+ * 4/6/8/9/10/12, threads per block) that shape is used without timing;
  * ESDP_EINVAL if it cannot be built for the context's assets.  The results
  * of an earlier esdp_solve are discarded (the timed launches reuse the
  * context's workspace): policy, EV, bid curves and esdp_grad answer

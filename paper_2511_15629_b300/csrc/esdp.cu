@@ -530,7 +530,7 @@ int plan_default(esdp_ctx* c, const std::vector<int>& ids, Plan* plan) {
   int best_rc = ESDP_EINVAL;
   double best_score = 1e300;
   Plan best;
-  for (int R : {8, 10, 12, 6, 4}) {
+  for (int R : {8, 10, 12, 9, 6, 4}) {
     for (int block : {256, 512, 384, 128}) {
       Plan p;
       std::string keep = c->err;
@@ -1394,7 +1394,7 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   CK(cudaEventCreate(&e1), "event");
   double best_ms = 1e300;
   int best_R = c->main.shape.R, best_block = c->main.shape.block;
-  for (int R : {4, 6, 8, 10, 12}) {
+  for (int R : {4, 6, 8, 9, 10, 12}) {
     for (int block : {128, 256, 384, 512}) {
       Plan p;
       std::string keep = c->err;

@@ -10,7 +10,7 @@ namespace esdp {
 
 // Rows of the SoC grid a thread owns in the banded max-plus (its register
 // window), one launch uses one value.
-constexpr int kRowsPerThreadChoices[] = {4, 6, 8, 10, 12};
+constexpr int kRowsPerThreadChoices[] = {4, 6, 8, 9, 10, 12};
 constexpr int kMaxBlock = 512;
 constexpr int kMaxWaits = 64;     // neighbour tiles a work item may wait on
 

@@ -10,9 +10,8 @@
 //      that read its rows and the tile holding the reference row have
 //      published EV_t;
 //   2. stages EV_t rows [s0 - D_dis, s1 + D_chg + R) of every mode in shared
-//      memory with TMA bulk copies (rows outside the grid are -inf: the
-//      infeasibility mask of Alg. 1), overlapped with building the payoff
-//      table r[m][k][a] = price[t][k] e_a - cost[a] (- switch cost);
+//      memory with 16-byte cp.async copies by every thread (rows outside the
+//      grid are -inf: the infeasibility mask of Alg. 1);
 //   3. runs the banded max-plus: a thread owns R consecutive rows of one
 //      (m, k) and slides a register window of EV values over the action band
 //      (two evaluations per 3-input max), tracking the winning chunk of R
@@ -219,7 +218,6 @@ struct Smem {
   float* delta;    // [K] level correction of the stage
   float* ref;      // EV'_t[ref]
   int* abort;
-  uint64_t* bar;   // EV tile bulk copies
   uint64_t* barP;  // transposed P bulk copy
   float *Ah, *Al;  // tcgen05 A operand: V' rows, tf32 hi and lo parts
   uint64_t* barM;  // tcgen05 products of the EV contraction
@@ -529,6 +527,7 @@ __device__ void expectation_tc(const SweepParams& p, const AssetDev& as, const W
   tc_before_sync();
 }
 
+
 __device__ __forceinline__ void expectation(const SweepParams& p, const AssetDev& as,
                                             const WorkItem& w, int te, const Smem& sm,
                                             uint32_t& parity_m) {
@@ -550,14 +549,13 @@ __device__ __forceinline__ void expectation(const SweepParams& p, const AssetDev
     expectation_rows<1>(as, w, te, Ps, Vs, dst);
 }
 
-// Release the item's EV rows: they are read by bulk copies (async proxy) of
-// other CTAs, hence the proxy fence before the release store.
+// Release the item's EV rows.  Other CTAs read them with cp.async or plain
+// loads (generic proxy) after an acquire of the flag, so the barrier and one
+// release store order them; a reader through bulk copies (async proxy) would
+// also need a proxy fence here.
 __device__ __forceinline__ void publish(int* flag, int v) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    st_release(flag, v);
-  }
+  if (threadIdx.x == 0) st_release(flag, v);
 }
 
 // Wait until every neighbour tile and the reference tile have published at
@@ -650,11 +648,18 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
     nm[j] = make_float2(max3f(best[j].x, x.x, y.x), max3f(best[j].y, x.y, y.y));
   }
 #pragma unroll
-  for (int i = 2; i < R; i += 2) {
+  for (int i = 2; i + 1 < R; i += 2) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const float2 x = add2(rr[i], wv[i + j]), y = add2(rr[i + 1], wv[i + 1 + j]);
       nm[j] = make_float2(max3f(nm[j].x, x.x, y.x), max3f(nm[j].y, x.y, y.y));
+    }
+  }
+  if constexpr ((R & 1) != 0) {  // an odd R: the chunk's last action on its own
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float2 x = add2(rr[R - 1], wv[R - 1 + j]);
+      nm[j] = make_float2(fmaxf(nm[j].x, x.x), fmaxf(nm[j].y, x.y));
     }
   }
 #pragma unroll
@@ -697,14 +702,13 @@ struct Deferred {
 // One stage of one work item.  Returns false if the launch is abandoned.
 template <int R>
 __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
-                           const WorkItem& w, int it, int g, const Smem& sm, uint32_t& parity,
+                           const WorkItem& w, int it, int g, const Smem& sm,
                            uint32_t& parity_p, uint32_t& parity_m, bool p_pref,
                            const StageScalars& pre, const Deferred& def) {
   const int t = as.t_hi - g;
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const float NEG = -CUDART_INF_F;
-  const bool tma = (K & 3) == 0;
   const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
 
   // 0. inputs of the stage: the bulk copy of P_{t-1} and the per-thread
@@ -730,18 +734,21 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
   }
   PHASE_MARK(1);
 
-  // 2. EV_t tile: bulk copies of the rows inside the grid, -inf outside
+  // 2. EV_t tile: copies of the rows inside the grid, -inf outside
   const float* ev_t = ev_ptr(as, t);
   const int g0row = w.s0 - as.D_dis;
   const int lo = max(g0row, 0), hi = min(g0row + rows, N);
-  if (tma) {
-    if (tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const uint32_t bytes = (uint32_t)(hi - lo) * K * 4u;
-      mbar_expect_tx(sm.bar, bytes * M);
-      for (int m = 0; m < M; ++m)
-        bulk_load(sm.Es + ((size_t)m * rows + (lo - g0row)) * K, ev_t + ((size_t)m * N + lo) * K,
-                  bytes, sm.bar);
+  if ((K & 3) == 0) {
+    // 16-byte cp.async copies by every thread (generic proxy: the producers
+    // need no proxy fence before their release)
+    const int n16 = (hi - lo) * (K >> 2);
+    for (int m = 0; m < M; ++m) {
+      const float4* src = reinterpret_cast<const float4*>(ev_t + ((size_t)m * N + lo) * K);
+      float4* dst = reinterpret_cast<float4*>(sm.Es + ((size_t)m * rows + (lo - g0row)) * K);
+      for (int i = tid; i < n16; i += nth)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + i)),
+                     "l"(src + i)
+                     : "memory");
     }
   } else {
     for (int m = 0; m < M; ++m) {
@@ -783,10 +790,6 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
     if (w.tile == 0) as.evoff[(size_t)(t - 1) * K + tid] = cr;
   }
   if (tid == K && (K & 1)) sm.lam[K] = 0.f;  // pad state of an odd K
-  if (tma) {
-    if (tid == 0 && !mbar_wait_bounded(sm.bar, parity, p)) *(volatile int*)sm.abort = 1;
-    parity ^= 1u;
-  }
   if (p_bulk) {
     if (tid == 0 && !mbar_wait_bounded(sm.barP, parity_p, p)) *(volatile int*)sm.abort = 1;
     parity_p ^= 1u;
@@ -831,7 +834,7 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
       bx[j] = -1;
       by[j] = -1;
     }
-    auto chunk = [&](int c) {
+    auto chunk = [&](int c, float2 (&bst)[R], int (&cx)[R], int (&cy)[R]) {
       const bool second = c >= n0;
       const int u0 = (second ? c - n0 : c) * R;
       const int a0 = second ? g1.a0 : g0.a0;
@@ -839,18 +842,18 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
       const int toff = second ? n0 * R : 0;
       const float2* eb =
           reinterpret_cast<const float2*>(sm.Es + ((size_t)src * rows + b * R + a0 + u0) * Ke) + kp;
-      maxplus_chunk<R>(eb, Kh, ec + toff + u0, lam, c, best, bx, by);
+      maxplus_chunk<R>(eb, Kh, ec + toff + u0, lam, c, bst, cx, cy);
     };
     // two chunks per iteration where the registers allow: independent loads
     // and max chains in flight
     int c = c_lo;
     if constexpr (R <= 8) {
       for (; c + 1 < c_hi; c += 2) {
-        chunk(c);
-        chunk(c + 1);
+        chunk(c, best, bx, by);
+        chunk(c + 1, best, bx, by);
       }
     }
-    for (; c < c_hi; ++c) chunk(c);
+    for (; c < c_hi; ++c) chunk(c, best, bx, by);
     PHASE_MARK(3);
     // merge the parts of each cell: the larger value, on equal values the
     // earlier chunk (the parts hold increasing action ranges)
@@ -867,49 +870,75 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
     // winning chunk that reproduces the max (the same two round-to-nearest
     // operations as the packed evaluation); V'_t = max + c_{t+1} rho_t[k] - c_t
     if (active) {
-      // one entry: its max bj and winning chunk c
-      auto recover = [&](int j, int h, float bj, int c) {
+      // argmax of one entry (row j, state k0 + h) from its max bj and winning
+      // chunk c, without stores, so that the loads of all of a lane's entries
+      // can be in flight together; -1 for padding entries
+      auto argmax_of = [&](int j, int h, float bj, int c) -> int {
+        const int row = b * R + j, k = k0 + h;
+        if (c < 0 || k >= K || row >= Wt) return -1;
+        const float lk = h ? lam.y : lam.x;
+        const bool second = c >= n0;
+        const int u0 = (second ? c - n0 : c) * R;
+        const int a0 = second ? g1.a0 : g0.a0;
+        const int src = second ? g1.src : g0.src;
+        const int toff = second ? n0 * R : 0;
+        const float* eb = sm.Es + ((size_t)src * rows + row + a0 + u0) * Ke + k;
+        const float2* ep = ec + toff + u0;
+        float v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const float2 ei = ep[i];
+          v[i] = fmaf(lk, ei.x, ei.y) + eb[(size_t)i * Ke];
+        }
+        int first = R - 1;
+#pragma unroll
+        for (int i = R - 1; i >= 0; --i)
+          if (v[i] == bj) first = i;
+        return a0 + u0 + first;
+      };
+      // V'_t and the argmax of an entry into the V tile (and the tcgen05
+      // operand parts) and the index tile; the asset fields are read once,
+      // before any store (the descriptor lives in shared memory)
+      const int tcv = as.tc;
+      float* Vs = sm.Vs;
+      float* Ah = sm.Ah;
+      float* Al = sm.Al;
+      auto store = [&](int j, int h, float bj, int arg) {
         const int row = b * R + j, k = k0 + h;
         if (k >= K || row >= Wt) return;
-        const float lk = h ? lam.y : lam.x;
-        int arg = -1;
-        if (c >= 0) {
-          const bool second = c >= n0;
-          const int u0 = (second ? c - n0 : c) * R;
-          const int a0 = second ? g1.a0 : g0.a0;
-          const int src = second ? g1.src : g0.src;
-          const int toff = second ? n0 * R : 0;
-          const float* eb = sm.Es + ((size_t)src * rows + row + a0 + u0) * Ke + k;
-          const float2* ep = ec + toff + u0;
-          float v[R];
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float2 ei = ep[i];
-            v[i] = fmaf(lk, ei.x, ei.y) + eb[(size_t)i * Ke];
-          }
-          int first = R - 1;
-#pragma unroll
-          for (int i = R - 1; i >= 0; --i)
-            if (v[i] == bj) first = i;
-          arg = a0 + u0 + first;
+        const float v = bj + sm.delta[k];
+        Vs[(m * W + row) * Kv + k] = v;
+        if (tcv) {
+          uint32_t hi, lo;
+          split_tf32(v, hi, lo);
+          const int o = tc_offset(m * Wt + row, k, K, kCmA);
+          Ah[o] = __uint_as_float(hi);
+          Al[o] = __uint_as_float(lo);
         }
-        put_v(sm.Vs, sm.Ah, sm.Al, as, Wt, m, row, k, bj + sm.delta[k]);
         Xi[(m * W + row) * K + k] = arg;
       };
       if (G == 2) {
         // lane `part` takes state k0 + part of every row
+        int arg[R];
 #pragma unroll
         for (int j = 0; j < R; ++j)
-          recover(j, part, part ? best[j].y : best[j].x, part ? by[j] : bx[j]);
-      } else if (G == 4) {
+          arg[j] = argmax_of(j, part, part ? best[j].y : best[j].x, part ? by[j] : bx[j]);
+#pragma unroll
+        for (int j = 0; j < R; ++j) store(j, part, part ? best[j].y : best[j].x, arg[j]);
+      } else if (G == 4 && (R & 1) == 0) {
         // lane `part` takes state k0 + (part & 1) of the rows j = part/2 + 2i
         const int h = part & 1, jo = part >> 1;
+        int arg[R / 2];
+        float bv[R / 2];
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) {
           const float2 bb = jo ? best[2 * i + 1] : best[2 * i];
           const int cx = jo ? bx[2 * i + 1] : bx[2 * i], cy = jo ? by[2 * i + 1] : by[2 * i];
-          recover(2 * i + jo, h, h ? bb.y : bb.x, h ? cy : cx);
+          bv[i] = h ? bb.y : bb.x;
+          arg[i] = argmax_of(2 * i + jo, h, bv[i], h ? cy : cx);
         }
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) store(2 * i + jo, h, bv[i], arg[i]);
       } else {
 #pragma unroll 2
         for (int e = part; e < 2 * R; e += G) {
@@ -922,7 +951,7 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
               bj = h ? best[jj].y : best[jj].x;
               c = h ? by[jj] : bx[jj];
             }
-          recover(j, h, bj, c);
+          store(j, h, bj, argmax_of(j, h, bj, c));
         }
       }
     }
@@ -1012,7 +1041,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
 #ifdef ESDP_PHASE_CLOCKS
   PhaseClock pc;
 #endif
-  uint32_t parity = 0, parity_p = 0, parity_m = 0;
+  uint32_t parity_p = 0, parity_m = 0;
   // the work item's asset descriptor lives in shared memory: the loops that
   // store to global memory then need not reload its fields
   auto load_asset = [&](int a) {
@@ -1085,8 +1114,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(PHASE_ARG p, as, w, it, g, sm, parity, parity_p, parity_m, pref, pre,
-                         def))
+      if (!item_stage<R>(PHASE_ARG p, as, w, it, g, sm, parity_p, parity_m, pref, pre, def))
         return;
       def.it = -1;
       publish(p.flags + as.flag_base + w.tile, g + 2);
@@ -1137,7 +1165,6 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   __shared__ float s_delta[128];
   __shared__ double s_rho[128];
   __shared__ float s_ref;
-  __shared__ __align__(8) uint64_t s_bar;
   __shared__ __align__(8) uint64_t s_barP;
   __shared__ __align__(8) uint64_t s_barM;
   __shared__ uint32_t s_tmem;
@@ -1156,12 +1183,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   sm.rho = s_rho;
   sm.ref = &s_ref;
   sm.abort = &s_abort;
-  sm.bar = &s_bar;
   sm.barP = &s_barP;
   sm.barM = &s_barM;
   if (threadIdx.x == 0) {
     s_abort = 0;
-    mbar_init(&s_bar);
     mbar_init(&s_barP);
     mbar_init(&s_barM);
   }
@@ -1268,6 +1293,7 @@ cudaError_t launch_sweep(const SweepShape& s, const SweepParams& p, cudaStream_t
     case 4: return launch_R<4>(s, p, stream);
     case 6: return launch_R<6>(s, p, stream);
     case 8: return launch_R<8>(s, p, stream);
+    case 9: return launch_R<9>(s, p, stream);
     case 10: return launch_R<10>(s, p, stream);
     case 12: return launch_R<12>(s, p, stream);
     default: return cudaErrorInvalidValue;
@@ -1279,6 +1305,7 @@ int sweep_max_blocks_per_sm(int R, int block, size_t smem) {
     case 4: return max_blocks_R<4>(block, smem);
     case 6: return max_blocks_R<6>(block, smem);
     case 8: return max_blocks_R<8>(block, smem);
+    case 9: return max_blocks_R<9>(block, smem);
     case 10: return max_blocks_R<10>(block, smem);
     case 12: return max_blocks_R<12>(block, smem);
     default: return 0;

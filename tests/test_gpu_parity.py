@@ -547,7 +547,7 @@ def test_autotune_keeps_results():
     V1b = s.solve_instances()[0]
     np.testing.assert_array_equal(V1, V1b)
     info = s.launch_info()
-    assert info["grid"] >= 1 and info["rows_per_thread"] in (4, 6, 8, 10, 12)
+    assert info["grid"] >= 1 and info["rows_per_thread"] in (4, 6, 8, 9, 10, 12)
 
 
 # ------------------------------------------------- bid-curve exact predicate
@@ -629,8 +629,8 @@ def test_autotune_shape_pin(monkeypatch):
     assert ei.value.code == E.ESDP_EINVAL
 
 
-@pytest.mark.parametrize("R,block,K", [(4, 256, 20), (6, 512, 20), (8, 256, 16), (10, 384, 20),
-                                       (12, 256, 12)])
+@pytest.mark.parametrize("R,block,K", [(4, 256, 20), (6, 512, 20), (8, 256, 16), (9, 512, 20),
+                                       (9, 256, 16), (10, 384, 20), (12, 256, 12)])
 def test_every_rows_per_thread_variant(monkeypatch, R, block, K):
     """Each compiled rows-per-thread variant of the sweep (pinned through
     ESDP_SHAPE) matches the oracle's values and policies; K = 16 takes the
