@@ -628,13 +628,13 @@ __device__ void build_columns(const SweepParams& p, const AssetDev& as, float2* 
 // Each running maximum takes the chunk's R candidates in one chain of 3-input
 // maxima; the chunk index is recorded where a maximum strictly rises, so the
 // earliest chunk that attains it is kept.
-template <int R>
-__device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const float2* ecp,
-                                              float2 lam, int c, float2 (&best)[R], int (&bx)[R],
-                                              int (&by)[R]) {
-  float2 wv[2 * R - 1];
-#pragma unroll
-  for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
+// The chunk's window is wv[OFF .. OFF + 2R - 1) of registers the caller
+// loaded (one chunk's 2R - 1 rows, or two consecutive chunks' 3R - 1).
+template <int R, int OFF, int NW>
+__device__ __forceinline__ void maxplus_core(const float2 (&wv)[NW], const float2* ecp, float2 lam,
+                                             int c, float2 (&best)[R], int (&bx)[R],
+                                             int (&by)[R]) {
+  static_assert(OFF + 2 * R - 1 <= NW, "window");
   float2 rr[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -644,21 +644,21 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
   float2 nm[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) {
-    const float2 x = add2(rr[0], wv[j]), y = add2(rr[1], wv[j + 1]);
+    const float2 x = add2(rr[0], wv[OFF + j]), y = add2(rr[1], wv[OFF + j + 1]);
     nm[j] = make_float2(max3f(best[j].x, x.x, y.x), max3f(best[j].y, x.y, y.y));
   }
 #pragma unroll
   for (int i = 2; i + 1 < R; i += 2) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const float2 x = add2(rr[i], wv[i + j]), y = add2(rr[i + 1], wv[i + 1 + j]);
+      const float2 x = add2(rr[i], wv[OFF + i + j]), y = add2(rr[i + 1], wv[OFF + i + 1 + j]);
       nm[j] = make_float2(max3f(nm[j].x, x.x, y.x), max3f(nm[j].y, x.y, y.y));
     }
   }
   if constexpr ((R & 1) != 0) {  // an odd R: the chunk's last action on its own
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const float2 x = add2(rr[R - 1], wv[R - 1 + j]);
+      const float2 x = add2(rr[R - 1], wv[OFF + R - 1 + j]);
       nm[j] = make_float2(fmaxf(nm[j].x, x.x), fmaxf(nm[j].y, x.y));
     }
   }
@@ -668,6 +668,29 @@ __device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const fl
     if (nm[j].y > best[j].y) by[j] = c;
     best[j] = nm[j];
   }
+}
+
+template <int R>
+__device__ __forceinline__ void maxplus_chunk(const float2* eb, int Kh, const float2* ecp,
+                                              float2 lam, int c, float2 (&best)[R], int (&bx)[R],
+                                              int (&by)[R]) {
+  float2 wv[2 * R - 1];
+#pragma unroll
+  for (int x = 0; x < 2 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
+  maxplus_core<R, 0>(wv, ecp, lam, c, best, bx, by);
+}
+
+// Two consecutive chunks c, c + 1 of one action segment: their windows
+// overlap in R - 1 rows, so 3R - 1 rows are loaded once for both.
+template <int R>
+__device__ __forceinline__ void maxplus_pair(const float2* eb, int Kh, const float2* ecp,
+                                             float2 lam, int c, float2 (&best)[R], int (&bx)[R],
+                                             int (&by)[R]) {
+  float2 wv[3 * R - 1];
+#pragma unroll
+  for (int x = 0; x < 3 * R - 1; ++x) wv[x] = eb[(size_t)x * Kh];
+  maxplus_core<R, 0>(wv, ecp, lam, c, best, bx, by);
+  maxplus_core<R, R>(wv, ecp + R, lam, c + 1, best, bx, by);
 }
 
 // Inputs of stage t of work item `it` that do not depend on other tiles:
@@ -799,11 +822,12 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
   PHASE_MARK(2);
 
   // 3. banded max-plus.  A cell is (pair of price states, block of R rows,
-  //    mode); its chunks of R actions are split into G = parts contiguous
-  //    ranges.  A warp holds L = 32/G cells in each of the G ranges (lane =
-  //    cell slot + L * part), so the parts of a cell meet in one warp and are
-  //    merged by shuffles.  Each lane slides a register window of EV pairs
-  //    over its chunks: two evaluations per packed add and per 3-input max.
+  //    mode); its chunks of R actions are split over G = parts thread groups
+  //    (contiguous ranges, or every G-th chunk, see below).  A warp holds
+  //    L = 32/G cells in each of the G groups (lane = cell slot + L * part),
+  //    so the parts of a cell meet in one warp and are merged by shuffles.
+  //    Each lane slides a register window of EV pairs over its chunks: two
+  //    evaluations per packed add and per 3-input max.
   const int Kh = Ke >> 1;
   const int G = as.parts, lgL = 5 - (31 - __clz(G)), L = 32 >> (31 - __clz(G));
   const int ncell = Kh * as.nb * M;
@@ -823,7 +847,12 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
     segments(as, m, g0, g1);
     const int n0 = round_up(g0.len, R) / R;
     const int nc = n0 + round_up(g1.len, R) / R;
-    const int c_lo = part * nc / G, c_hi = active ? (part + 1) * nc / G : c_lo;
+    // R >= 6: each part takes a contiguous range of chunks (consecutive
+    // chunks share R - 1 window rows); R < 6: part p takes the chunks p,
+    // p + G, p + 2G, ..., so that the lanes of a warp read rows R apart and
+    // their shared-memory loads spread over the banks
+    const int c_lo = R >= 6 ? part * nc / G : part;
+    const int c_hi = !active ? c_lo : R >= 6 ? (part + 1) * nc / G : nc;
     const float2* ec = sm.EC + m * rs;
     const float2 lam = make_float2(sm.lam[k0], sm.lam[k0 + 1]);
     float2 best[R];
@@ -847,16 +876,38 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
     // two chunks per iteration where the registers allow: independent loads
     // and max chains in flight
     int c = c_lo;
-    if constexpr (R <= 8) {
+    if constexpr (R >= 6 && R <= 8) {
+      // (for R = 4 the per-chunk windows measured faster: 1.86 vs 1.90 ms on
+      // the two-mode 5-minute asset)
       for (; c + 1 < c_hi; c += 2) {
-        chunk(c, best, bx, by);
-        chunk(c + 1, best, bx, by);
+        if ((c >= n0) == (c + 1 >= n0)) {
+          // both chunks in one action segment: one window of 3R - 1 rows
+          const bool second = c >= n0;
+          const int u0 = (second ? c - n0 : c) * R;
+          const int a0 = second ? g1.a0 : g0.a0;
+          const int src = second ? g1.src : g0.src;
+          const int toff = second ? n0 * R : 0;
+          const float2* eb = reinterpret_cast<const float2*>(
+                                 sm.Es + ((size_t)src * rows + b * R + a0 + u0) * Ke) + kp;
+          maxplus_pair<R>(eb, Kh, ec + toff + u0, lam, c, best, bx, by);
+        } else {
+          chunk(c, best, bx, by);
+          chunk(c + 1, best, bx, by);
+        }
       }
     }
-    for (; c < c_hi; ++c) chunk(c, best, bx, by);
+    if constexpr (R < 6) {
+      for (; c + G < c_hi; c += 2 * G) {
+        chunk(c, best, bx, by);
+        chunk(c + G, best, bx, by);
+      }
+      for (; c < c_hi; c += G) chunk(c, best, bx, by);
+    } else {
+      for (; c < c_hi; ++c) chunk(c, best, bx, by);
+    }
     PHASE_MARK(3);
     // merge the parts of each cell: the larger value, on equal values the
-    // earlier chunk (the parts hold increasing action ranges)
+    // earlier chunk
     for (int d = L; d < 32; d <<= 1) {
 #pragma unroll
       for (int j = 0; j < R; ++j) {
