@@ -62,7 +62,9 @@ def parse():
                     help="per-stage cycles of each sweep phase (config3 and config2) from the "
                          "library built with per-phase clock counters; prints one JSON line")
     ap.add_argument("--profile-case", default="",
-                    help="config3-64 | config2 | table3-20h: one solve inside the NVTX range 'esdp_profile' "
+                    help="config3 | config3-64 | config3-64-A101 | config2 | config5-grad | table3-20h: "
+                         "one solve inside "
+                         "the NVTX range 'esdp_profile' "
                          "(for ncu --nvtx --nvtx-include esdp_profile/)")
     return ap.parse_args()
 
@@ -752,13 +754,24 @@ def run_profile_case(name):
     import torch
     from paper_2511_15629_b300 import esdp as E
     from paper_2511_15629_b300 import instances as I
-    if name == "config3-64":
+    if name == "config3":
+        inst = I.config3()
+    elif name == "config3-64":
         full = I.config3()
         n = 64
         inst = I.Instance("config3_last64", n, full.N, full.K, full.A, full.D_dis, full.D_chg, 1,
                           full.s_max, full.tau, full.eta_c, full.eta_d, 0.0,
                           full.price[-n:].copy(), full.trans[-n:].copy(), full.cost,
                           full.terminal, s0=full.s0)
+    elif name == "config3-64-A101":
+        # the same stages with the middle 101 actions: the difference of two
+        # captures isolates the max-plus loop's cost per chunk of actions
+        full = I.config3()
+        n = 64
+        inst = I.Instance("config3_last64_A101", n, full.N, full.K, 101, 50, 50, 1, full.s_max,
+                          full.tau, full.eta_c, full.eta_d, 0.0, full.price[-n:].copy(),
+                          full.trans[-n:].copy(), full.cost[50:151].copy(), full.terminal,
+                          s0=full.s0)
     elif name == "config2":
         inst = I.config2()
     elif name == "config5-grad":
