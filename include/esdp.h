@@ -204,7 +204,10 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
  * keep the fastest (results are cached per shape class for the process).
  * The paper has no counterpart (its sweep is one library broadcast per
  * stage); the shapes only change how the Bellman step of eq. 5 is tiled,
- * not its result up to float32 rounding of the EV contraction.
+ * not its result up to float32 rounding of the EV contraction.  Launches
+ * whose assets all have K = 63 or 64 use a kernel variant with the shared
+ * EV row stride fixed at compile time (same results; ESDP_NO_KH=1 pins the
+ * general variant).
  * With the environment variable ESDP_SHAPE="R,block" (rows per thread
  * 4/6/8/9/10/12, threads per block) that shape is used without timing;
  * ESDP_EINVAL if it cannot be built for the context's assets.  The results

@@ -239,6 +239,11 @@ double item_cost(const esdp_asset& a, const AssetChoice& ch, int s0, int s1, int
 int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int grid_cap,
                Plan* plan) {
   plan->shape.R = R;
+  {
+    std::vector<esdp_asset> launch_assets;
+    for (int id : ids) launch_assets.push_back(c->assets[id]);
+    plan->shape.kh = getenv("ESDP_NO_KH") ? 0 : sweep_kh(launch_assets.begin(), launch_assets.end());
+  }
   plan->shape.block = block;
   plan->asset_ids = ids;
   plan->adev.clear();
@@ -343,7 +348,7 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     return fail(c, ESDP_EINVAL, "shared memory plan of %zu bytes exceeds the limit",
                 plan->shape.smem);
   // co-resident grid (cooperative launch) and LPT assignment of the items
-  int per_sm = sweep_max_blocks_per_sm(R, block, plan->shape.smem);
+  int per_sm = sweep_max_blocks_per_sm(R, plan->shape.kh, block, plan->shape.smem);
   if (per_sm < 1) return fail(c, ESDP_EINVAL, "sweep kernel does not fit on an SM");
   int grid = std::min((int)plan->items.size(), std::min(grid_cap, per_sm * c->n_sm));
   grid = std::max(grid, 1);

@@ -196,13 +196,23 @@ inline int pick_parts(int cells, int block, int chunks) {
 // Launch shape of one sweep.
 struct SweepShape {
   int R = 8;
+  int kh = 0;       // 32: every asset has K = 63 or 64 (the kernel variant with a fixed EV row stride)
   int block = 256;
   int grid = 0;
   size_t smem = 0;
 };
 
 cudaError_t launch_sweep(const SweepShape& shape, const SweepParams& p, cudaStream_t stream);
-int sweep_max_blocks_per_sm(int R, int block, size_t smem);
+int sweep_max_blocks_per_sm(int R, int kh, int block, size_t smem);
+// The kernel variant for a launch's assets: 32 when every asset has
+// ceil(K / 2) = 32 price-state pairs, else 0 (row stride read at run time).
+template <typename It>
+inline int sweep_kh(It first, It last) {
+  if (first == last) return 0;
+  for (It i = first; i != last; ++i)
+    if ((i->K + 1) / 2 != 32) return 0;
+  return 32;
+}
 // Instance preparation for a launch: row sums (double) of every transition
 // matrix and, where the asset has a buffer for it, the transposed padded copy
 // ptrans[t][k2][k] = trans[t][k][k2].

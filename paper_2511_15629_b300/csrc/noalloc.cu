@@ -132,7 +132,8 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
     return msg(err, err_len, ESDP_EINVAL, buf);
   }
   const size_t smem = L.bytes;
-  const int per_sm = sweep_max_blocks_per_sm(R, block, smem);
+  const int kh = (a.K + 1) / 2 == 32 ? 32 : 0;
+  const int per_sm = sweep_max_blocks_per_sm(R, kh, block, smem);
   if (per_sm < 1) return msg(err, err_len, ESDP_ECUDA, "sweep kernel does not fit on an SM");
   const int grid = std::min(tiles, per_sm * n_sm);
 
@@ -244,6 +245,7 @@ extern "C" int esdp_solve_noalloc(const esdp_asset* asset, const float* price, c
   sp.sm_X = L.X;
   SweepShape shape;
   shape.R = R;
+  shape.kh = kh;
   shape.block = block;
   shape.grid = grid;
   shape.smem = smem;

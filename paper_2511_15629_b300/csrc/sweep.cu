@@ -723,7 +723,7 @@ struct Deferred {
 };
 
 // One stage of one work item.  Returns false if the launch is abandoned.
-template <int R>
+template <int R, int KH>
 __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
                            const WorkItem& w, int it, int g, const Smem& sm,
                            uint32_t& parity_p, uint32_t& parity_m, bool p_pref,
@@ -732,7 +732,10 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
   const int K = as.K, M = as.M, N = as.N, rows = as.rows, rs = as.rs, W = as.W;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const float NEG = -CUDART_INF_F;
-  const int Ke = K + (K & 1);  // EV tile row stride: price states in pairs
+  // EV tile row stride: price states in pairs (a compile-time constant in
+  // the launches whose assets all have K = 2 KH - 1 or 2 KH, so that the
+  // register window is loaded with immediate offsets)
+  const int Ke = KH > 0 ? 2 * KH : K + (K & 1);
 
   // 0. inputs of the stage: the bulk copy of P_{t-1} and the per-thread
   // scalars (price, row sum, running level) may already be in flight, issued
@@ -828,7 +831,7 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
   //    so the parts of a cell meet in one warp and are merged by shuffles.
   //    Each lane slides a register window of EV pairs over its chunks: two
   //    evaluations per packed add and per 3-input max.
-  const int Kh = Ke >> 1;
+  const int Kh = KH > 0 ? KH : Ke >> 1;
   const int G = as.parts, lgL = 5 - (31 - __clz(G)), L = 32 >> (31 - __clz(G));
   const int ncell = Kh * as.nb * M;
   int* Xi = reinterpret_cast<int*>(sm.Xs);
@@ -1086,7 +1089,7 @@ __device__ void item_outputs(const SweepParams& p, const AssetDev& as, const Wor
 
 // The persistent sweep of one CTA: its work items for every stage.  Returns
 // early (uniformly over the CTA) when the launch is abandoned.
-template <int R>
+template <int R, int KH>
 __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, AssetDev& s_as) {
   const int i0 = p.cta_items[blockIdx.x], i1 = p.cta_items[blockIdx.x + 1];
 #ifdef ESDP_PHASE_CLOCKS
@@ -1165,7 +1168,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
         build_columns<R>(p, as, sm.EC);  // read after the barriers of the stage
         cols_asset = w.asset;
       }
-      if (!item_stage<R>(PHASE_ARG p, as, w, it, g, sm, parity_p, parity_m, pref, pre, def))
+      if (!item_stage<R, KH>(PHASE_ARG p, as, w, it, g, sm, parity_p, parity_m, pref, pre, def))
         return;
       def.it = -1;
       publish(p.flags + as.flag_base + w.tile, g + 2);
@@ -1206,7 +1209,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& p, const Smem& sm, 
 #endif
 }
 
-template <int R>
+template <int R, int KH>
 __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -1254,7 +1257,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) sweep_kernel(const SweepParams p
   __syncthreads();
   tc_after_sync();
   sm.tmem = p.tmem_cols > 0 ? s_tmem : 0u;
-  sweep_run<R>(p, sm, s_as);
+  sweep_run<R, KH>(p, sm, s_as);
   tc_before_sync();
   __syncthreads();
   if (p.tmem_cols > 0 && threadIdx.x < 32) {
@@ -1304,9 +1307,9 @@ __global__ void rowsum_kernel(const AssetDev* assets, const float* trans) {
   }
 }
 
-template <int R>
+template <int R, int KH>
 cudaError_t launch_R(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
-  auto fn = sweep_kernel<R>;
+  auto fn = sweep_kernel<R, KH>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
   SweepParams pp = p;
@@ -1315,9 +1318,9 @@ cudaError_t launch_R(const SweepShape& s, const SweepParams& p, cudaStream_t str
                                      stream);
 }
 
-template <int R>
+template <int R, int KH>
 int max_blocks_R(int block, size_t smem) {
-  auto fn = sweep_kernel<R>;
+  auto fn = sweep_kernel<R, KH>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int n = 0;
@@ -1340,25 +1343,48 @@ cudaError_t launch_rowsums(const AssetDev* d_assets, int n_assets, int max_rows,
 }
 
 cudaError_t launch_sweep(const SweepShape& s, const SweepParams& p, cudaStream_t stream) {
+  if (s.kh == 32) {
+    switch (s.R) {
+      case 4: return launch_R<4, 32>(s, p, stream);
+      case 6: return launch_R<6, 32>(s, p, stream);
+      case 8: return launch_R<8, 32>(s, p, stream);
+      case 9: return launch_R<9, 32>(s, p, stream);
+      case 10: return launch_R<10, 32>(s, p, stream);
+      case 12: return launch_R<12, 32>(s, p, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (s.kh != 0) return cudaErrorInvalidValue;
   switch (s.R) {
-    case 4: return launch_R<4>(s, p, stream);
-    case 6: return launch_R<6>(s, p, stream);
-    case 8: return launch_R<8>(s, p, stream);
-    case 9: return launch_R<9>(s, p, stream);
-    case 10: return launch_R<10>(s, p, stream);
-    case 12: return launch_R<12>(s, p, stream);
+    case 4: return launch_R<4, 0>(s, p, stream);
+    case 6: return launch_R<6, 0>(s, p, stream);
+    case 8: return launch_R<8, 0>(s, p, stream);
+    case 9: return launch_R<9, 0>(s, p, stream);
+    case 10: return launch_R<10, 0>(s, p, stream);
+    case 12: return launch_R<12, 0>(s, p, stream);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int sweep_max_blocks_per_sm(int R, int block, size_t smem) {
+int sweep_max_blocks_per_sm(int R, int kh, int block, size_t smem) {
+  if (kh == 32) {
+    switch (R) {
+      case 4: return max_blocks_R<4, 32>(block, smem);
+      case 6: return max_blocks_R<6, 32>(block, smem);
+      case 8: return max_blocks_R<8, 32>(block, smem);
+      case 9: return max_blocks_R<9, 32>(block, smem);
+      case 10: return max_blocks_R<10, 32>(block, smem);
+      case 12: return max_blocks_R<12, 32>(block, smem);
+      default: return 0;
+    }
+  }
   switch (R) {
-    case 4: return max_blocks_R<4>(block, smem);
-    case 6: return max_blocks_R<6>(block, smem);
-    case 8: return max_blocks_R<8>(block, smem);
-    case 9: return max_blocks_R<9>(block, smem);
-    case 10: return max_blocks_R<10>(block, smem);
-    case 12: return max_blocks_R<12>(block, smem);
+    case 4: return max_blocks_R<4, 0>(block, smem);
+    case 6: return max_blocks_R<6, 0>(block, smem);
+    case 8: return max_blocks_R<8, 0>(block, smem);
+    case 9: return max_blocks_R<9, 0>(block, smem);
+    case 10: return max_blocks_R<10, 0>(block, smem);
+    case 12: return max_blocks_R<12, 0>(block, smem);
     default: return 0;
   }
 }

@@ -188,6 +188,24 @@ def test_config3_tail_full_parity():
     full_check(_c3_last(12), keep_ev=True)
 
 
+def test_fixed_row_stride_variant_equals_runtime_stride(monkeypatch):
+    """K = 64 assets run the sweep variant whose EV tile row stride is a
+    compile-time constant; the variant that reads it at run time (pinned
+    with ESDP_NO_KH) gives the same bits."""
+    inst = _c3_last(6)
+    a = solve_gpu(inst)[1]
+    monkeypatch.setenv("ESDP_NO_KH", "1")
+    b = solve_gpu(inst)[1]
+    np.testing.assert_array_equal(a, b)
+    odd = I.random_instance(97, 4, 400, 63, 30, 25, 2, neg_prob=0.2, cost="nonconvex")
+    c = solve_gpu(odd)[1]
+    monkeypatch.delenv("ESDP_NO_KH")
+    d = solve_gpu(odd)[1]
+    np.testing.assert_array_equal(c, d)
+    r = O.solve(odd, nthreads=NTHREADS, keep_policy=False)
+    assert_values(d, r["V1"], _scale(r["V1"]))
+
+
 def test_config3_full_horizon_sampled_stages():
     """The C3 sweep in its benchmark launch shape (all 2016 stages, keep EV).
     Each sampled stage is checked against the oracle's Bellman step taken
