@@ -267,7 +267,8 @@ struct OccParams {
   float* post;            // [C][M][N][K], written by the kernel
   unsigned long long* post_fx;  // [C][M][N][K] the scatter's fixed-point sums, zero on entry
   float fx_e;             // fixed-point scale (a power of two) of the rho * e_a terms
-  int own_smem;           // set by the launcher: own converted rows kept in shared memory
+  int own_smem;           // set by the launcher: own converted and occupancy rows in shared memory
+  int n_cost_copies;      // set by the launcher: copies of the shared per-action cost sums
   double* d_price;        // [T][K] (accumulated)
   double* acc;            // [5]: d_eta_c, d_eta_d, (two unused slots), d_switch
   double* d_cost;         // [A] (accumulated)

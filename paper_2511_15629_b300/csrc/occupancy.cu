@@ -31,6 +31,8 @@
 // |e_a| so that they have the same range.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/esdp.h"
 #include "esdp_internal.h"
 
@@ -132,9 +134,14 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   double* sacc = osm;                                       // [8] segment accumulators
   double* wacc = osm + 8;                                   // [8 warps][3] stage warp sums
   unsigned long long* skx = reinterpret_cast<unsigned long long*>(osm + 32);  // [K] dprice
-  unsigned long long* scx = skx + p.K;                      // [A] cost partials (segment)
-  float* Ps = reinterpret_cast<float*>(scx + p.A);          // [K][K]
-  float* spost = Ps + p.K * p.K;  // [grid_rows][K] own converted rows (if own_smem)
+  // [n_cc][A] cost partials of the segment: thread tid adds into copy
+  // tid % n_cc, so that the many states that take the same action (full
+  // charge, idle, full discharge) do not all hit one shared address
+  unsigned long long* scx = skx + p.K;
+  const int n_cc = p.n_cost_copies;
+  float* Ps0 = reinterpret_cast<float*>(scx + (size_t)n_cc * p.A);  // [2][K][K]: P_t, P_{t+1}
+  float* spost = Ps0 + 2 * p.K * p.K;  // [grid_rows][K] own converted rows (if own_smem)
+  float* srho = spost + p.grid_rows * p.K;  // [grid_rows][K] own occupancy rows (if own_smem)
   __shared__ int s_abort;
   const int K = p.K, N = p.N, M = p.M, MN = M * N;
   const size_t MNK = (size_t)MN * K;
@@ -143,26 +150,43 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   const int r1 = min(MN, r0 + p.grid_rows);
   // d rho lam delta / eta_c^2 per charging step, d rho lam delta per discharging step
   const float coef_c = (float)(p.delta / (p.eta_c * p.eta_c)), coef_d = (float)p.delta;
+  // own occupancy rows: in shared memory for the whole segment when they
+  // fit (the scatter reads and the contraction writes only these rows)
+  float* rho = p.own_smem ? srho - r0 * K : p.rho;
+  const double inv_fx_e = 1.0 / (double)p.fx_e;  // a power of two: exact
   if (tid == 0) s_abort = 0;
-  for (int a = tid; a < p.A; a += nth) scx[a] = 0ull;
+  for (int a = tid; a < n_cc * p.A; a += nth) scx[a] = 0ull;
   if (tid < 8) sacc[tid] = 0.0;  // summed over the segment
+  if (p.own_smem)
+    for (int i = r0 * K + tid; i < r1 * K; i += nth) srho[i - r0 * K] = p.rho[i];
+  {  // P of the first stage; every later P_{t+1} is copied during stage t
+    const float* P = p.trans + (size_t)(p.t_lo - 1) * K * K;
+    for (int i = tid; i < K * K; i += nth) Ps0[i] = P[i];
+  }
   __syncthreads();
   int epoch = 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
+    float* Ps = Ps0 + (ts & 1) * K * K;
     for (int i = tid; i < K; i += nth) skx[i] = 0ull;
-    {  // P_t for the contraction: its load overlaps the scatter
-      const float* P = p.trans + (size_t)(t - 1) * K * K;
-      for (int i = tid; i < K * K; i += nth) Ps[i] = P[i];
+    if (t < p.t_hi) {  // P_{t+1} into the other buffer, waited for at the end of the stage
+      const float* P = p.trans + (size_t)t * K * K;
+      float* Pn = Ps0 + ((ts + 1) & 1) * K * K;
+      for (int i = tid; i < K * K; i += nth)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(Pn + i)),
+                     "l"(P + i)
+                     : "memory");
     }
     __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
     unsigned long long* post_fx = p.post_fx + (size_t)ts * MNK;
+    unsigned long long* scx_t = scx + (size_t)(tid % n_cc) * p.A;
     const float* price_t = p.price + (size_t)(t - 1) * K;
     float dc = 0.f, dd = 0.f, dsw = 0.f;
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
-      const float rho = p.rho[i];
-      if (rho == 0.f) continue;
+      const float rv = rho[i];
+      if (rv == 0.f) continue;
       const int row = i / K, k = i - row * K;
       const int m = row / N, s = row - m * N;
       const size_t pi = (size_t)ts * MNK + i;
@@ -170,18 +194,18 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
                                         : reinterpret_cast<const int*>(p.policy)[pi];
       const int d = a - p.D_dis;
       if (a < 0 || a >= p.A || s + d < 0 || s + d >= N ||  // not a feasible stored action,
-          !(fabsf(rho) <= kFxMaxRho)) {                     // or outside the fixed-point range
+          !(fabsf(rv) <= kFxMaxRho)) {                      // or outside the fixed-point range
         atomicCAS(p.status, 0, ESDP_ENUMERIC);
         continue;
       }
       const int m2 = (M == 2) ? (d < 0 ? 0 : (d > 0 ? 1 : m)) : 0;
-      atomicAdd(post_fx + ((size_t)m2 * N + s + d) * K + k, to_fx(rho, kFxRho));
+      atomicAdd(post_fx + ((size_t)m2 * N + s + d) * K + k, to_fx(rv, kFxRho));
       const float lam = price_t[k];
-      atomicAdd(&skx[k], to_fx(rho * p.e[a], p.fx_e));
-      if (d > 0) dc = fmaf(rho * lam, (float)d * coef_c, dc);
-      if (d < 0) dd = fmaf(rho * lam, (float)(-d) * coef_d, dd);
-      atomicAdd(&scx[a], to_fx(-rho, kFxRho));
-      if (M == 2 && m == 1 && d < 0) dsw -= rho;
+      atomicAdd(&skx[k], to_fx(rv * p.e[a], p.fx_e));
+      if (d > 0) dc = fmaf(rv * lam, (float)d * coef_c, dc);
+      if (d < 0) dd = fmaf(rv * lam, (float)(-d) * coef_d, dd);
+      atomicAdd(&scx_t[a], to_fx(-rv, kFxRho));
+      if (M == 2 && m == 1 && d < 0) dsw -= rv;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -208,13 +232,19 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
         for (int q = 0; q < 8; ++q) p.part_acc[(size_t)blockIdx.x * 8 + q] = sacc[q];
     }
     double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
-    for (int i = tid; i < K; i += nth) pr[i] = (double)(long long)skx[i] / (double)p.fx_e;
+    for (int i = tid; i < K; i += nth) pr[i] = (double)(long long)skx[i] * inv_fx_e;
     if (t == p.t_hi)
-      for (int a = tid; a < p.A; a += nth)
-        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)(long long)scx[a] * kFxRhoInv;
+      for (int a = tid; a < p.A; a += nth) {
+        unsigned long long sum = 0ull;  // the copies in order (integer: exact)
+        for (int q = 0; q < n_cc; ++q) sum += scx[(size_t)q * p.A + a];
+        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)(long long)sum * kFxRhoInv;
+      }
     ++epoch;
     publish_stage(p.flags, epoch);
-    if (!wait_sources(p, r0, r1, epoch, &s_abort)) return;
+    if (!wait_sources(p, r0, r1, epoch, &s_abort)) {
+      asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
+      return;
+    }
     // own rows of the post-decision occupancy, complete: fixed point to
     // float, for dJ/dP and (in shared memory when they fit) the contraction
     for (int i = r0 * K + tid; i < r1 * K; i += nth) {
@@ -228,14 +258,16 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       const int row = i / K, k2 = i - row * K;
       float acc = 0.f;
       if (p.own_smem) {
-        const float* pr = spost + (size_t)(row - r0) * K;
-        for (int k = 0; k < K; ++k) acc = fmaf(pr[k], Ps[k * K + k2], acc);
+        const float* prw = spost + (size_t)(row - r0) * K;
+        for (int k = 0; k < K; ++k) acc = fmaf(prw[k], Ps[k * K + k2], acc);
       } else {
-        const float* pr = post + (size_t)row * K;
-        for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(pr + k), Ps[k * K + k2], acc);
+        const float* prw = post + (size_t)row * K;
+        for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(prw + k), Ps[k * K + k2], acc);
       }
-      p.rho[i] = acc;
+      rho[i] = acc;
+      if (p.own_smem && t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // P_{t+1} has landed
     __syncthreads();
   }
 }
@@ -397,12 +429,15 @@ cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream)
 }
 
 cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream_t stream) {
-  // segment sums, 8 warps x 3 stage sums, fixed-point K + A sums, P_t, and
-  // the own converted rows when they fit
-  const size_t base = 32 * sizeof(double) + (size_t)(p.K + p.A) * sizeof(unsigned long long) +
-                      (size_t)p.K * p.K * sizeof(float);
-  const size_t own = (size_t)p.grid_rows * p.K * sizeof(float);
+  // segment sums, 8 warps x 3 stage sums, fixed-point K sums and copies of
+  // the A cost sums, P_t and P_{t+1}, and (when they fit) the own converted
+  // rows and the own occupancy rows
   OccParams pp = p;
+  pp.n_cost_copies = (int)std::max<long long>(1, std::min<long long>(8, 16384 / std::max(1, p.A)));
+  const size_t base = 32 * sizeof(double) +
+                      ((size_t)p.K + (size_t)pp.n_cost_copies * p.A) * sizeof(unsigned long long) +
+                      2 * (size_t)p.K * p.K * sizeof(float);
+  const size_t own = 2 * (size_t)p.grid_rows * p.K * sizeof(float);
   pp.own_smem = base + own <= 160 * 1024 ? 1 : 0;
   const size_t smem = base + (pp.own_smem ? own : 0);
   cudaError_t e = cudaFuncSetAttribute(occ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
