@@ -258,8 +258,21 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       const int row = i / K, k2 = i - row * K;
       float acc = 0.f;
       if (p.own_smem) {
+        // in ascending k, one fma per term; the loads of eight terms are
+        // issued ahead of their fmas
         const float* prw = spost + (size_t)(row - r0) * K;
-        for (int k = 0; k < K; ++k) acc = fmaf(prw[k], Ps[k * K + k2], acc);
+        int k = 0;
+        for (; k + 8 <= K; k += 8) {
+          float a8[8], b8[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            a8[j] = prw[k + j];
+            b8[j] = Ps[(k + j) * K + k2];
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc = fmaf(a8[j], b8[j], acc);
+        }
+        for (; k < K; ++k) acc = fmaf(prw[k], Ps[k * K + k2], acc);
       } else {
         const float* prw = post + (size_t)row * K;
         for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(prw + k), Ps[k * K + k2], acc);
