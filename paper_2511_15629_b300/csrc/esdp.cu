@@ -102,7 +102,9 @@ struct esdp_ctx {
   bool solved = false;
   std::vector<int> prep_tc;       // per asset: tc flag of its last P preparation (-1: none)
   Plan main;
-  std::vector<Plan> solo;         // per-asset plans for the gradient recompute
+  // per asset: launch plans of the gradient's segment re-sweeps, keyed by
+  // the number of segments swept together in one launch
+  std::vector<std::map<int, Plan>> seg_plans;
   std::string err;
   unsigned long long timeout_ns = 5ull * 1000 * 1000 * 1000;
   // ESDP_TIME_SWEEP: events recorded around the sweep launch of esdp_solve
@@ -731,7 +733,7 @@ int esdp_create(const esdp_asset* assets, int32_t n_assets, uint32_t flags, esdp
   std::iota(ids.begin(), ids.end(), 0);
   if ((rc = plan_default(c, ids, &c->main))) return rc;
   bind_main(c, &c->main);
-  c->solo.resize(c->assets.size());
+  c->seg_plans.resize(c->assets.size());
   c->prep_tc.assign(c->assets.size(), -1);
   return ESDP_OK;
 }
@@ -773,7 +775,8 @@ void esdp_destroy(esdp_ctx* c) {
   for (cudaEvent_t& e : c->ev_sweep)
     if (e) cudaEventDestroy(e);
   free_plan(&c->main);
-  for (Plan& p : c->solo) free_plan(&p);
+  for (auto& m : c->seg_plans)
+    for (auto& kv : m) free_plan(&kv.second);
   for (void* p : c->allocs) cudaFree(p);
   cudaFree(c->bid_scr);
   cudaFree(c->grad_scr);
@@ -1147,15 +1150,30 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   if (a.ckpt_every > 0 && T > C && !c->d_ckpt[asset])
     return fail(c, ESDP_ESTATE, "no checkpoints kept");
   int rc;
-  // solo launch plan for this asset (same shape rules as the main plan)
-  Plan& sp = c->solo[asset];
-  if (sp.adev.empty()) {
-    if ((rc = plan_default(c, std::vector<int>{asset}, &sp))) return rc;
+  const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
+  // The segments' re-sweeps are independent of one another (each starts
+  // from its own checkpoint), so B of them run as the assets of one
+  // persistent launch; the policies and values of those B segments are held
+  // at once.  B: ESDP_GRAD_SEGMENTS, else as many as 1 GiB of slots holds.
+  const size_t slot_bytes =
+      L * C * pb + L * (C + 1) * 4 + 2 * L * 4 + (size_t)(T + 2) * 8 + 4 * 256;
+  int B = (int)std::max<size_t>(1, std::min<size_t>(nseg, (size_t(1) << 30) / slot_bytes));
+  if (const char* f = getenv("ESDP_GRAD_SEGMENTS")) B = std::max(1, std::min(nseg, atoi(f)));
+  const int ngrp = (nseg + B - 1) / B;
+  B = (nseg + ngrp - 1) / ngrp;  // groups of equal size but the last
+  const int b_last = nseg - (ngrp - 1) * B;
+  // launch plans of B and of b_last segments (same shape rules as the main plan)
+  Plan* gplan[2] = {nullptr, nullptr};
+  for (int q = 0; q < 2; ++q) {
+    const int b = q == 0 ? B : b_last;
+    Plan& pl = c->seg_plans[asset][b];
+    if (pl.adev.empty() && (rc = plan_default(c, std::vector<int>(b, asset), &pl))) return rc;
+    gplan[q] = &pl;
   }
   // workspace: carved from the context's gradient scratch (kept across calls)
   void *seg_pol, *seg_v, *seg_post, *rho, *ev2, *dprice64, *acc, *bar, *d_mu, *dJ, *dtr, *dpr,
-      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs, *dtpart, *dtmass, *post_fx;
-  const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
+      *dcost64, *dco, *opart, *opart_cost, *opart_acc, *dsegs, *dtpart, *dtmass, *post_fx,
+      *seg_off;
   const int MN = M * N;
   int ogrid = std::min(c->n_sm, std::max(1, (MN + 7) / 8));  // occupancy CTAs
   const int orows = (MN + ogrid - 1) / ogrid;
@@ -1163,14 +1181,14 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   {
     void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
                      &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
-                     &opart_acc, &dsegs, &dtpart, &dtmass, &post_fx};
-    const size_t sizes[] = {L * C * pb, L * (C + 1) * 4, L * C * 4, L * 4, 2 * L * 4,
+                     &opart_acc, &dsegs, &dtpart, &dtmass, &post_fx, &seg_off};
+    const size_t sizes[] = {L * C * pb * B, L * (C + 1) * 4 * B, L * C * 4, L * 4, 2 * L * 4 * B,
                             (size_t)T * K * 8, 8 * 8, (size_t)ogrid * 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
                             (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
                             (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
                             (size_t)nseg * sizeof(AssetDev), (size_t)C * 4 * K * K * 8,
-                            (size_t)C * 4 * K * 8, L * C * 8};
+                            (size_t)C * 4 * K * 8, L * C * 8, (size_t)(T + 2) * 8 * B};
     size_t total = 0;
     for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
     if (total > c->grad_scr_bytes) {
@@ -1185,7 +1203,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
       c->grad_scr_bytes = total;
     }
     char* q = (char*)c->grad_scr;
-    for (int i = 0; i < 21; ++i) {
+    for (int i = 0; i < 22; ++i) {
       *outs[i] = q;
       q += (sizes[i] + 255) / 256 * 256;
     }
@@ -1212,48 +1230,66 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
   const float* cost = c->last_cost + c->off_cost[asset];
   const float* terminal = c->last_terminal + c->off_terminal[asset];
   // the re-sweeps' asset descriptors, one per segment, uploaded together (a
-  // host upload per segment would drain the stream before each re-sweep)
-  std::vector<AssetDev> segs(nseg, sp.adev[0]);
+  // host upload per segment would drain the stream before each re-sweep);
+  // segment j runs as launch asset j % B of group j / B, in slot j % B of
+  // the policy, value, EV and level buffers (the levels the re-sweep writes
+  // go to the slot: the solve's own c_t stay as they are)
+  std::vector<AssetDev> segs(nseg);
   for (int j = 0; j < nseg; ++j) {
+    const int g = j / B, i = j % B;
     const int t_lo = 1 + j * C, t_hi = std::min(T, (j + 1) * C);
     AssetDev& d = segs[j];
+    d = gplan[g == ngrp - 1 ? 1 : 0]->adev[i];
     d.t_hi = t_hi;
     d.t_lo = t_lo;
     d.v_start = (t_hi == T) ? nullptr : c->d_ckpt[asset] + (size_t)j * L;
     d.c_start = (t_hi == T) ? nullptr : c->d_off[asset] + t_hi + 1;
-    d.ev = (float*)ev2;
+    d.ev = (float*)ev2 + (size_t)i * 2 * L;
     d.ev_keep = 0;
-    d.policy = seg_pol;
+    d.policy = (char*)seg_pol + (size_t)i * L * C * pb;
     d.policy_bytes = pb;
     d.policy_t_base = t_lo;
     d.ckpt_every = 0;
     d.ckpt = nullptr;
-    d.v_keep = (float*)seg_v;
+    d.v_keep = (float*)seg_v + (size_t)i * L * (C + 1);
+    d.off = (double*)seg_off + (size_t)i * (T + 2);
   }
-  if (!sp.uploaded) {  // work items and CTA lists, once per context
-    if ((rc = upload_plan(c, &sp, st))) {
+  for (Plan* pl : gplan)
+    if (!pl->uploaded && (rc = upload_plan(c, pl, st))) {  // once per context
       release();
       return rc;
     }
-  }
   if ((e = cudaMemcpyAsync(dsegs, segs.data(), (size_t)nseg * sizeof(AssetDev),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cfail(e, "segment descriptors");
   for (int j = 0; j < nseg; ++j) {
     const int t_lo = 1 + j * C, t_hi = std::min(T, (j + 1) * C);
     const int nt = t_hi - t_lo + 1;
-    sp.n_steps = nt;
-    // the last solve prepared the row sums and P of these transition matrices;
-    // P again only if this plan's tile size picks another EV path (layout)
-    const bool prep = j == 0 && c->prep_tc[asset] != sp.adev[0].tc;
-    if ((rc = run_plan(c, &sp, c->last_price, c->last_trans, c->last_cost, c->last_terminal,
-                       nullptr, st, prep, (const AssetDev*)dsegs + j))) {
-      release();
-      return rc;
+    const int g = j / B, i = j % B;
+    if (i == 0) {  // the group's re-sweeps
+      Plan* pl = gplan[g == ngrp - 1 ? 1 : 0];
+      pl->n_steps = 0;
+      for (int jj = j; jj < std::min(nseg, j + B); ++jj)
+        pl->n_steps = std::max(pl->n_steps, segs[jj].t_hi - segs[jj].t_lo + 1);
+      // the last solve prepared the row sums and P of these transition
+      // matrices; P again (once: the launch's assets are one asset) only if
+      // this plan's tile size picks another EV path (operand layout)
+      if (c->prep_tc[asset] != pl->adev[0].tc) {
+        if ((e = launch_rowsums(pl->d_assets, 1, pl->max_rows, c->last_trans, st)) != cudaSuccess)
+          return cfail(e, "row sums");
+        c->prep_tc[asset] = pl->adev[0].tc;
+      }
+      if ((rc = run_plan(c, pl, c->last_price, c->last_trans, c->last_cost, c->last_terminal,
+                         nullptr, st, false, (const AssetDev*)dsegs + j))) {
+        release();
+        return rc;
+      }
     }
+    float* slot_v = (float*)seg_v + (size_t)i * L * (C + 1);
+    const void* slot_pol = (const char*)seg_pol + (size_t)i * L * C * pb;
     // V_{t_hi+1} after the segment's values, so V_{t+1} of stage t sits at t - t_lo + 1
     const float* vend = segs[j].v_start ? segs[j].v_start : terminal;
-    if ((e = cudaMemcpyAsync((float*)seg_v + (size_t)nt * L, vend, L * 4, cudaMemcpyDeviceToDevice,
+    if ((e = cudaMemcpyAsync(slot_v + (size_t)nt * L, vend, L * 4, cudaMemcpyDeviceToDevice,
                              st)) != cudaSuccess)
       return cfail(e, "segment copy");
     cudaMemsetAsync(post_fx, 0, L * nt * 8, st);
@@ -1271,7 +1307,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.trans = trans;
     op.cost = cost;
     op.e = c->d_e + c->off_e[asset];
-    op.policy = seg_pol;
+    op.policy = slot_pol;
     op.policy_bytes = pb;
     op.rho = (float*)rho;
     op.post = (float*)seg_post;
@@ -1293,7 +1329,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     dp.MN = MN;
     dp.K = K;
     dp.post = (const float*)seg_post;
-    dp.vnext = (const float*)seg_v + L;
+    dp.vnext = slot_v + L;
     dp.cnext = c->d_off[asset] + t_lo + 1;
     dp.d_trans = (float*)dtr + (size_t)(t_lo - 1) * K * K;
     dp.part = (double*)dtpart;
@@ -1375,9 +1411,9 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
     free_plan(&c->main);
     if ((rc = build_plan(c, ids, R, block, c->n_sm, &c->main))) return rc;
     bind_main(c, &c->main);
-    for (Plan& sp : c->solo) {
-      free_plan(&sp);
-      sp = Plan();
+    for (auto& m : c->seg_plans) {
+      for (auto& kv : m) free_plan(&kv.second);
+      m.clear();
     }
     return ESDP_OK;
   }
@@ -1464,9 +1500,9 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   free_plan(&c->main);
   if ((rc = build_plan(c, ids, best_R, best_block, c->n_sm, &c->main))) return rc;
   bind_main(c, &c->main);
-  for (Plan& p : c->solo) {
-    free_plan(&p);
-    p = Plan();
+  for (auto& m : c->seg_plans) {
+    for (auto& kv : m) free_plan(&kv.second);
+    m.clear();
   }
   int status = 0;
   CK(cudaMemcpy(&status, c->d_status, 4, cudaMemcpyDeviceToHost), "status");

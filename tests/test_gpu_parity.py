@@ -366,6 +366,29 @@ def test_gradient_repeat_calls_agree():
         np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
 
 
+def test_gradient_segment_groups_agree(monkeypatch):
+    """The checkpoint segments are re-swept B at a time as the assets of one
+    launch (ESDP_GRAD_SEGMENTS = B; 5 segments: groups 5, 3 + 2, 2 + 2 + 1
+    and 1 at a time).  Every grouping gives the same bits: a segment's
+    recomputation does not depend on the segments launched beside it (K = 10
+    keeps every tile on the FP32 SIMT contraction)."""
+    inst = I.random_instance(57, 37, 260, 10, 12, 14, 2, neg_prob=0.2, switch_cost=3.0)
+    inst.s0 = 120
+    inst.ckpt_every = 8
+    inst.policy_bytes = 2
+    s, _ = solve_gpu(inst)
+    mu0 = np.full(inst.K, 1.0 / inst.K, np.float32)
+    ref = None
+    for b in ("5", "3", "2", "1"):
+        monkeypatch.setenv("ESDP_GRAD_SEGMENTS", b)
+        out = s.grad(0, mu0, extra=True)
+        if ref is None:
+            ref = out
+            continue
+        for x, y in zip(ref, out):
+            np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
+
+
 def test_gradient_rejects_occupancy_beyond_fixed_point_range():
     """An initial distribution with entries above 2^20 cannot be added in the
     scatter's fixed point: the call reports ESDP_ENUMERIC instead of
