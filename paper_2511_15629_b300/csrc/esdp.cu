@@ -1131,6 +1131,29 @@ __global__ void to_float_kernel(const double* src, float* dst, long long n) {
   if (i < n) dst[i] = (float)src[i];
 }
 
+// The gradient re-sweeps its checkpoint segments B at a time as the assets
+// of one persistent launch (they are independent: each starts from its own
+// checkpoint), holding the policies, values and post-decision occupancies of
+// those B segments at once:
+// B = ESDP_GRAD_SEGMENTS, else as many as 1 GiB of slots holds; the groups
+// have equal sizes except the last (b_last segments).
+void grad_groups(const esdp_asset& a, int* B_out, int* b_last_out, int* nseg_out) {
+  const int T = a.T;
+  const int C = a.ckpt_every > 0 ? std::min((int)a.ckpt_every, T) : T;
+  const int nseg = (T + C - 1) / C;
+  const size_t L = mnk_of(a);
+  const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
+  const size_t slot_bytes = L * C * pb + L * (C + 1) * 4 + L * C * 4 + 2 * L * 4 +
+                            (size_t)(T + 2) * 8 + (size_t)C * kDtSplit * (a.K + 1) * a.K * 8;
+  int B = (int)std::max<size_t>(1, std::min<size_t>(nseg, (size_t(1) << 30) / slot_bytes));
+  if (const char* f = getenv("ESDP_GRAD_SEGMENTS")) B = std::max(1, std::min(nseg, atoi(f)));
+  const int ngrp = (nseg + B - 1) / B;
+  B = (nseg + ngrp - 1) / ngrp;
+  *B_out = B;
+  *b_last_out = nseg - (ngrp - 1) * B;
+  *nseg_out = nseg;
+}
+
 }  // namespace
 
 extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J,
@@ -1151,17 +1174,9 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     return fail(c, ESDP_ESTATE, "no checkpoints kept");
   int rc;
   const int pb = a.policy_bytes > 0 ? a.policy_bytes : 4;
-  // The segments' re-sweeps are independent of one another (each starts
-  // from its own checkpoint), so B of them run as the assets of one
-  // persistent launch; the policies and values of those B segments are held
-  // at once.  B: ESDP_GRAD_SEGMENTS, else as many as 1 GiB of slots holds.
-  const size_t slot_bytes =
-      L * C * pb + L * (C + 1) * 4 + 2 * L * 4 + (size_t)(T + 2) * 8 + 4 * 256;
-  int B = (int)std::max<size_t>(1, std::min<size_t>(nseg, (size_t(1) << 30) / slot_bytes));
-  if (const char* f = getenv("ESDP_GRAD_SEGMENTS")) B = std::max(1, std::min(nseg, atoi(f)));
+  int B, b_last, nseg_g;
+  grad_groups(a, &B, &b_last, &nseg_g);
   const int ngrp = (nseg + B - 1) / B;
-  B = (nseg + ngrp - 1) / ngrp;  // groups of equal size but the last
-  const int b_last = nseg - (ngrp - 1) * B;
   // launch plans of B and of b_last segments (same shape rules as the main plan)
   Plan* gplan[2] = {nullptr, nullptr};
   for (int q = 0; q < 2; ++q) {
@@ -1182,13 +1197,13 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     void** outs[] = {&seg_pol, &seg_v, &seg_post, &rho, &ev2, &dprice64, &acc,
                      &bar, &d_mu, &dJ, &dtr, &dpr, &dcost64, &dco, &opart, &opart_cost,
                      &opart_acc, &dsegs, &dtpart, &dtmass, &post_fx, &seg_off};
-    const size_t sizes[] = {L * C * pb * B, L * (C + 1) * 4 * B, L * C * 4, L * 4, 2 * L * 4 * B,
+    const size_t sizes[] = {L * C * pb * B, L * (C + 1) * 4 * B, L * C * 4 * B, L * 4, 2 * L * 4 * B,
                             (size_t)T * K * 8, 8 * 8, (size_t)ogrid * 4, (size_t)K * 4, 8,
                             (size_t)T * K * K * 4, (size_t)T * K * 4, (size_t)a.A * 8,
                             (size_t)a.A * 4, (size_t)C * ogrid * K * 8,
                             (size_t)ogrid * a.A * 8, (size_t)ogrid * 8 * 8,
-                            (size_t)nseg * sizeof(AssetDev), (size_t)C * 4 * K * K * 8,
-                            (size_t)C * 4 * K * 8, L * C * 8, (size_t)(T + 2) * 8 * B};
+                            (size_t)nseg * sizeof(AssetDev), (size_t)C * B * kDtSplit * K * K * 8,
+                            (size_t)C * B * kDtSplit * K * 8, L * C * 8, (size_t)(T + 2) * 8 * B};
     size_t total = 0;
     for (size_t sz : sizes) total += (sz + 255) / 256 * 256;
     if (total > c->grad_scr_bytes) {
@@ -1310,7 +1325,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.policy = slot_pol;
     op.policy_bytes = pb;
     op.rho = (float*)rho;
-    op.post = (float*)seg_post;
+    op.post = (float*)seg_post + (size_t)i * L * C;
     op.post_fx = (unsigned long long*)post_fx;
     op.fx_e = c->fx_e[asset];
     op.d_price = (double*)dprice64;
@@ -1324,17 +1339,25 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.timeout_ns = c->timeout_ns;
     if ((e = launch_occupancy(op, grid, 256, st)) != cudaSuccess) return cfail(e, "occupancy");
     if ((e = launch_occ_reduce(op, grid, st)) != cudaSuccess) return cfail(e, "occupancy sums");
-    DTransParams dp{};
-    dp.n_t = nt;
-    dp.MN = MN;
-    dp.K = K;
-    dp.post = (const float*)seg_post;
-    dp.vnext = slot_v + L;
-    dp.cnext = c->d_off[asset] + t_lo + 1;
-    dp.d_trans = (float*)dtr + (size_t)(t_lo - 1) * K * K;
-    dp.part = (double*)dtpart;
-    dp.part_mass = (double*)dtmass;
-    if ((e = launch_dtrans(dp, st)) != cudaSuccess) return cfail(e, "dtrans");
+    // dJ/dP of the group's stages once its last segment's occupancy is in
+    // (one launch over all of them: enough blocks to fill the SMs)
+    if (i == B - 1 || j == nseg - 1) {
+      const int g_lo = 1 + (j - i) * C;
+      DTransParams dp{};
+      dp.n_t = t_hi - g_lo + 1;
+      dp.MN = MN;
+      dp.K = K;
+      dp.post = (const float*)seg_post;
+      dp.vnext = (const float*)seg_v + L;
+      dp.seg_len = C;
+      dp.seg_stride = (long long)(L * (C + 1));
+      dp.cnext = c->d_off[asset] + g_lo + 1;
+      dp.d_trans = (float*)dtr + (size_t)(g_lo - 1) * K * K;
+      dp.n_split = kDtSplit;
+      dp.part = (double*)dtpart;
+      dp.part_mass = (double*)dtmass;
+      if ((e = launch_dtrans(dp, st)) != cudaSuccess) return cfail(e, "dtrans");
+    }
   }
   const long long nP = (long long)T * K;
   to_float_kernel<<<(unsigned)((nP + 255) / 256), 256, 0, st>>>((const double*)dprice64,
@@ -1388,6 +1411,120 @@ extern "C" int esdp_objective(esdp_ctx* c, int32_t asset, const float* mu0, doub
 
 // ---------------------------------------------------------------- autotuner
 
+namespace {
+
+struct ZeroInputs {
+  const float *price, *trans, *cost, *terminal;
+};
+
+// Time every launch shape for the launch assets `ids` over their last
+// `t_short` stages (zero inputs: the cost of the sweep does not depend on the
+// values), best of four launches after a warm-up; records the fastest in the
+// tuning cache (keyed by the assets' shapes) and returns it.
+void tune_launch(esdp_ctx* c, const std::vector<int>& ids, int t_short, const ZeroInputs& z,
+                 cudaStream_t st, int* best_R, int* best_block) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  // copies of one asset (the gradient's segment groups) each get their own
+  // levels and reference entries, and P is prepared once for them
+  const bool copies = ids.size() > 1 && ids[0] == ids[1];
+  void* lvl_scr = nullptr;
+  if (copies) {
+    const esdp_asset& a = c->assets[ids[0]];
+    const size_t per = (size_t)(a.T + 2) * 8 + (size_t)a.T * a.K * 8 + (size_t)(a.T + 2) * 4;
+    if (cudaMalloc(&lvl_scr, per * ids.size()) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return;
+    }
+  }
+  double best_ms = 1e300;
+  for (int R : {4, 6, 8, 9, 10, 12}) {
+    for (int block : {128, 256, 384, 512}) {
+      Plan p;
+      std::string keep = c->err;
+      if (build_plan(c, ids, R, block, c->n_sm, &p)) {
+        c->err = keep;
+        continue;
+      }
+      char* q = (char*)lvl_scr;
+      for (AssetDev& d : p.adev) {
+        d.t_lo = std::max(1, d.t_hi - t_short + 1);
+        d.ev_keep = 0;
+        d.policy = nullptr;
+        d.policy_bytes = 0;
+        d.ckpt = nullptr;
+        d.v_keep = nullptr;
+        if (copies) {
+          d.off = (double*)q;
+          q += (size_t)(d.T + 2) * 8;
+          d.evoff = (double*)q;
+          q += (size_t)d.T * d.K * 8;
+          d.ref_hist = (float*)q;
+          q += (size_t)(d.T + 2) * 4;
+        }
+      }
+      // double-buffered EV scratch per launch asset
+      std::vector<float*> evs;
+      bool ok = true;
+      for (size_t j = 0; j < p.adev.size(); ++j) {
+        float* ev = nullptr;
+        if (cudaMalloc(&ev, 2 * mnk_of(c->assets[ids[j]]) * 4) != cudaSuccess) {
+          cudaGetLastError();
+          ok = false;
+          break;
+        }
+        evs.push_back(ev);
+        p.adev[j].ev = ev;
+      }
+      p.n_steps = 0;
+      for (const AssetDev& d : p.adev) p.n_steps = std::max(p.n_steps, d.t_hi - d.t_lo + 1);
+      double ms = 1e300;
+      if (ok && copies) {
+        ok = upload_plan(c, &p, st) == ESDP_OK &&
+             launch_rowsums(p.d_assets, 1, p.max_rows, z.trans, st) == cudaSuccess;
+        c->prep_tc[ids[0]] = p.adev[0].tc;
+      }
+      if (ok) {
+        for (int rep = 0; rep < 5 && ok; ++rep) {
+          cudaEventRecord(e0, st);
+          if (run_plan(c, &p, z.price, z.trans, z.cost, z.terminal, nullptr, st, !copies)) {
+            ok = false;
+            break;
+          }
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float f = 0.f;
+          cudaEventElapsedTime(&f, e0, e1);
+          if (rep > 0) ms = std::min(ms, (double)f);
+        }
+      }
+      cudaStreamSynchronize(st);
+      for (float* ev : evs) cudaFree(ev);
+      free_plan(&p);
+      if (ok && ms < best_ms) {
+        best_ms = ms;
+        *best_R = R;
+        *best_block = block;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(lvl_scr);
+  if (best_ms < 1e300) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[TuneKey{signature(c, ids)}] = {*best_R, *best_block};
+  }
+}
+
+}  // namespace
+
 extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   if (!c) return ESDP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1420,7 +1557,6 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   // time every candidate on zero inputs over a short horizon (the cost of
   // the sweep does not depend on the values): best of four launches after a
   // warm-up, so that run-to-run noise rarely decides between close shapes
-  const int t_short = 16;
   float *zp = nullptr, *zt = nullptr, *zc = nullptr, *zm = nullptr;
   int rc;
   if ((rc = dalloc(c, &zp, c->n_price)) || (rc = dalloc(c, &zt, c->n_trans)) ||
@@ -1430,72 +1566,26 @@ extern "C" int esdp_autotune(esdp_ctx* c, void* stream) {
   CK(cudaMemsetAsync(zt, 0, c->n_trans * 4, st), "tune");
   CK(cudaMemsetAsync(zc, 0, c->n_cost * 4, st), "tune");
   CK(cudaMemsetAsync(zm, 0, c->n_terminal * 4, st), "tune");
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0), "event");
-  CK(cudaEventCreate(&e1), "event");
-  double best_ms = 1e300;
+  const ZeroInputs z{zp, zt, zc, zm};
   int best_R = c->main.shape.R, best_block = c->main.shape.block;
-  for (int R : {4, 6, 8, 9, 10, 12}) {
-    for (int block : {128, 256, 384, 512}) {
-      Plan p;
-      std::string keep = c->err;
-      if (build_plan(c, ids, R, block, c->n_sm, &p)) {
-        c->err = keep;
-        continue;
+  tune_launch(c, ids, 16, z, st, &best_R, &best_block);
+  // the gradient's segment re-sweeps: B (and b_last) copies of an asset
+  // over C stages each
+  for (size_t id = 0; id < c->assets.size(); ++id) {
+    const esdp_asset& a = c->assets[id];
+    if (a.ckpt_every <= 0 || a.T <= a.ckpt_every) continue;
+    int B, b_last, nseg;
+    grad_groups(a, &B, &b_last, &nseg);
+    for (int b : {B, b_last}) {
+      const std::vector<int> seg_ids(b, (int)id);
+      bool have;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        have = g_tune_cache.count(TuneKey{signature(c, seg_ids)}) > 0;
       }
-      for (AssetDev& d : p.adev) {
-        d.t_lo = std::max(1, d.t_hi - t_short + 1);
-        d.ev_keep = 0;
-        d.policy = nullptr;
-        d.policy_bytes = 0;
-        d.ckpt = nullptr;
-        d.v_keep = nullptr;
-      }
-      // double-buffered EV scratch per asset
-      std::vector<float*> evs;
-      bool ok = true;
-      for (size_t j = 0; j < p.adev.size(); ++j) {
-        float* ev = nullptr;
-        if (cudaMalloc(&ev, 2 * mnk_of(c->assets[ids[j]]) * 4) != cudaSuccess) {
-          cudaGetLastError();
-          ok = false;
-          break;
-        }
-        evs.push_back(ev);
-        p.adev[j].ev = ev;
-      }
-      p.n_steps = 0;
-      for (const AssetDev& d : p.adev) p.n_steps = std::max(p.n_steps, d.t_hi - d.t_lo + 1);
-      double ms = 1e300;
-      if (ok) {
-        for (int rep = 0; rep < 5 && ok; ++rep) {
-          cudaEventRecord(e0, st);
-          if (run_plan(c, &p, zp, zt, zc, zm, nullptr, st)) {
-            ok = false;
-            break;
-          }
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-          float f = 0.f;
-          cudaEventElapsedTime(&f, e0, e1);
-          if (rep > 0) ms = std::min(ms, (double)f);
-        }
-      }
-      cudaStreamSynchronize(st);
-      for (float* ev : evs) cudaFree(ev);
-      free_plan(&p);
-      if (ok && ms < best_ms) {
-        best_ms = ms;
-        best_R = R;
-        best_block = block;
-      }
+      int R = best_R, block = best_block;
+      if (!have) tune_launch(c, seg_ids, std::min(16, (int)a.ckpt_every), z, st, &R, &block);
     }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[TuneKey{signature(c, ids)}] = {best_R, best_block};
   }
   free_plan(&c->main);
   if ((rc = build_plan(c, ids, best_R, best_block, c->n_sm, &c->main))) return rc;

@@ -287,12 +287,17 @@ cudaError_t launch_occ_reduce(const OccParams& p, int grid, cudaStream_t stream)
 struct DTransParams {
   int n_t, MN, K;
   const float* post;    // [n_t][MN][K]
-  const float* vnext;   // V'_{t+1} for the n_t stages: [n_t][MN][K]
+  const float* vnext;   // V'_{t+1} of stage ts (0-based) at vnext + (ts / seg_len) * seg_stride
+                        // + (ts % seg_len) * MN * K (segments of seg_len stages)
+  int seg_len;
+  long long seg_stride;
   const double* cnext;  // [n_t]: c_{t+1}, V_{t+1} = V'_{t+1} + c_{t+1}
   float* d_trans;       // [n_t][K][K]
-  double* part;         // [n_t][4][K][K] row-quarter partial sums (scratch)
-  double* part_mass;    // [n_t][4][K] row-quarter occupancy masses (scratch)
+  int n_split;          // row ranges per (stage, tile)
+  double* part;         // [n_t][n_split][K][K] row-range partial sums (scratch)
+  double* part_mass;    // [n_t][n_split][K] row-range occupancy masses (scratch)
 };
+constexpr int kDtSplit = 4;  // row ranges of the dJ/dP reduction
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream);
 
 }  // namespace esdp

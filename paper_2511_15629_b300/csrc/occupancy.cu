@@ -56,14 +56,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 // This CTA's scatter of stage `epoch` is complete: its atomics on the
-// post-decision occupancy are ordered before the flag (barrier, fence,
-// release store by one thread).
+// post-decision occupancy are ordered before the flag by the CTA barrier and
+// one release store at GPU scope (cumulative over what the barrier ordered
+// before it; a separate fence ahead of the release cost 0.6 us per stage).
 __device__ __forceinline__ void publish_stage(int* flags, int epoch) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release(flags + blockIdx.x, epoch);
-  }
+  if (threadIdx.x == 0) st_release(flags + blockIdx.x, epoch);
 }
 
 // Wait until every CTA that can scatter into this CTA's rows [r0, r1) has
@@ -121,6 +119,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr float kFxRho = 4294967296.f;  // 2^32 units per unit of occupancy mass
 constexpr double kFxRhoInv = 1.0 / 4294967296.0;
+constexpr int kPre = 4;  // entries per thread whose actions are loaded a stage ahead
 constexpr float kFxMaxRho = 1048576.f;  // 2^20: larger entries are reported
 
 __device__ __forceinline__ unsigned long long to_fx(float x, float scale) {
@@ -157,6 +156,7 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   if (tid == 0) s_abort = 0;
   for (int a = tid; a < n_cc * p.A; a += nth) scx[a] = 0ull;
   if (tid < 8) sacc[tid] = 0.0;  // summed over the segment
+  for (int i = tid; i < p.K; i += nth) skx[i] = 0ull;
   if (p.own_smem)
     for (int i = r0 * K + tid; i < r1 * K; i += nth) srho[i - r0 * K] = p.rho[i];
   {  // P of the first stage; every later P_{t+1} is copied during stage t
@@ -165,38 +165,35 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   }
   __syncthreads();
   int epoch = 0;
+  // the stored actions of a thread's first kPre entries are loaded one stage
+  // ahead, so that the scatter waits on no global load
+  const int e0 = r0 * K + tid, e1 = r1 * K;
+  auto action_at = [&](int ts_, int i) -> int {
+    const size_t pi = (size_t)ts_ * MNK + i;
+    return p.policy_bytes == 2 ? (int)__ldcg(reinterpret_cast<const short*>(p.policy) + pi)
+                               : __ldcg(reinterpret_cast<const int*>(p.policy) + pi);
+  };
+  int apre[kPre];
+#pragma unroll
+  for (int j = 0; j < kPre; ++j) apre[j] = e0 + j * nth < e1 ? action_at(0, e0 + j * nth) : 0;
   for (int t = p.t_lo; t <= p.t_hi; ++t) {
     const int ts = t - p.t_lo;
     float* Ps = Ps0 + (ts & 1) * K * K;
-    for (int i = tid; i < K; i += nth) skx[i] = 0ull;
-    if (t < p.t_hi) {  // P_{t+1} into the other buffer, waited for at the end of the stage
-      const float* P = p.trans + (size_t)t * K * K;
-      float* Pn = Ps0 + ((ts + 1) & 1) * K * K;
-      for (int i = tid; i < K * K; i += nth)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(Pn + i)),
-                     "l"(P + i)
-                     : "memory");
-    }
-    __syncthreads();
     float* post = p.post + (size_t)ts * MNK;
     unsigned long long* post_fx = p.post_fx + (size_t)ts * MNK;
     unsigned long long* scx_t = scx + (size_t)(tid % n_cc) * p.A;
     const float* price_t = p.price + (size_t)(t - 1) * K;
     float dc = 0.f, dd = 0.f, dsw = 0.f;
-    for (int i = r0 * K + tid; i < r1 * K; i += nth) {
+    auto scatter = [&](int i, int a) {
       const float rv = rho[i];
-      if (rv == 0.f) continue;
+      if (rv == 0.f) return;
       const int row = i / K, k = i - row * K;
       const int m = row / N, s = row - m * N;
-      const size_t pi = (size_t)ts * MNK + i;
-      const int a = p.policy_bytes == 2 ? (int)reinterpret_cast<const short*>(p.policy)[pi]
-                                        : reinterpret_cast<const int*>(p.policy)[pi];
       const int d = a - p.D_dis;
       if (a < 0 || a >= p.A || s + d < 0 || s + d >= N ||  // not a feasible stored action,
           !(fabsf(rv) <= kFxMaxRho)) {                      // or outside the fixed-point range
         atomicCAS(p.status, 0, ESDP_ENUMERIC);
-        continue;
+        return;
       }
       const int m2 = (M == 2) ? (d < 0 ? 0 : (d > 0 ? 1 : m)) : 0;
       atomicAdd(post_fx + ((size_t)m2 * N + s + d) * K + k, to_fx(rv, kFxRho));
@@ -206,6 +203,29 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       if (d < 0) dd = fmaf(rv * lam, (float)(-d) * coef_d, dd);
       atomicAdd(&scx_t[a], to_fx(-rv, kFxRho));
       if (M == 2 && m == 1 && d < 0) dsw -= rv;
+    };
+#pragma unroll
+    for (int j = 0; j < kPre; ++j)
+      if (e0 + j * nth < e1) scatter(e0 + j * nth, apre[j]);
+    for (int i = e0 + kPre * nth; i < e1; i += nth) scatter(i, action_at(ts, i));
+    // the scatter is complete once every thread is past the barrier of the
+    // release; the stage's partial sums are formed after it, while the
+    // sources are awaited
+    ++epoch;
+    publish_stage(p.flags, epoch);
+    if (t < p.t_hi) {
+      // P_{t+1} into the other buffer (its last reader, the contraction of
+      // stage t - 1, is behind the barrier), waited for at the end of the stage
+      const float* P = p.trans + (size_t)t * K * K;
+      float* Pn = Ps0 + ((ts + 1) & 1) * K * K;
+      for (int i = tid; i < K * K; i += nth)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(Pn + i)),
+                     "l"(P + i)
+                     : "memory");
+#pragma unroll
+      for (int j = 0; j < kPre; ++j)
+        if (e0 + j * nth < e1) apre[j] = action_at(ts + 1, e0 + j * nth);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -218,10 +238,25 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       wacc[(tid >> 5) * 3 + 1] = (double)dd;
       wacc[(tid >> 5) * 3 + 2] = (double)dsw;
     }
-    __syncthreads();
-    // this CTA's partials of the stage (and, once, of the segment's costs
-    // and accumulators): plain stores, added up after the launch in a fixed
-    // order; the warp sums are added in warp order
+    // this CTA's partials of the stage (and, once, of the segment's costs):
+    // plain stores, added up after the launch in a fixed order; a K sum is
+    // cleared by the thread that read it, before the next stage's scatter
+    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
+    for (int i = tid; i < K; i += nth) {
+      pr[i] = (double)(long long)skx[i] * inv_fx_e;
+      skx[i] = 0ull;
+    }
+    if (t == p.t_hi)
+      for (int a = tid; a < p.A; a += nth) {
+        unsigned long long sum = 0ull;  // the copies in order (integer: exact)
+        for (int q = 0; q < n_cc; ++q) sum += scx[(size_t)q * p.A + a];
+        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)(long long)sum * kFxRhoInv;
+      }
+    if (!wait_sources(p, r0, r1, epoch, &s_abort)) {
+      asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
+      return;
+    }
+    // the warp sums in warp order (written before the barrier of the wait)
     if (tid == 0) {
       for (int wq = 0; wq < (nth >> 5); ++wq) {
         sacc[0] += wacc[wq * 3 + 0];
@@ -231,30 +266,19 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       if (t == p.t_hi)
         for (int q = 0; q < 8; ++q) p.part_acc[(size_t)blockIdx.x * 8 + q] = sacc[q];
     }
-    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
-    for (int i = tid; i < K; i += nth) pr[i] = (double)(long long)skx[i] * inv_fx_e;
-    if (t == p.t_hi)
-      for (int a = tid; a < p.A; a += nth) {
-        unsigned long long sum = 0ull;  // the copies in order (integer: exact)
-        for (int q = 0; q < n_cc; ++q) sum += scx[(size_t)q * p.A + a];
-        p.part_cost[(size_t)blockIdx.x * p.A + a] = (double)(long long)sum * kFxRhoInv;
-      }
-    ++epoch;
-    publish_stage(p.flags, epoch);
-    if (!wait_sources(p, r0, r1, epoch, &s_abort)) {
-      asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
-      return;
-    }
     // own rows of the post-decision occupancy, complete: fixed point to
     // float, for dJ/dP and (in shared memory when they fit) the contraction
-    for (int i = r0 * K + tid; i < r1 * K; i += nth) {
+    for (int i = e0; i < e1; i += nth) {
       const float v = (float)((double)(long long)__ldcg(post_fx + i) * kFxRhoInv);
       post[i] = v;
       if (p.own_smem) spost[i - r0 * K] = v;
     }
     __syncthreads();
-    // contraction of the post-decision occupancy with P_t (own rows)
-    for (int i = r0 * K + tid; i < r1 * K; i += nth) {
+    // contraction of the post-decision occupancy with P_t (own rows); entry
+    // i of rho is written here and read by the next scatter in the same
+    // thread, and every other shared buffer of the next stage is reused only
+    // behind its release barrier, so no barrier closes the stage
+    for (int i = e0; i < e1; i += nth) {
       const int row = i / K, k2 = i - row * K;
       float acc = 0.f;
       if (p.own_smem) {
@@ -280,23 +304,21 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       rho[i] = acc;
       if (p.own_smem && t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // P_{t+1} has landed
-    __syncthreads();
+    asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's part of P_{t+1}
   }
 }
 
 // dJ/dP_t = post_t^T V_{t+1} over all rows (m, s): one block per (stage,
-// 32 x 32 tile of (k, k2), quarter of the rows).  Lane l of every warp owns
-// column k2 = 32 tx + l and keeps the 32 sums of its tile rows k = 32 ty + j
-// in registers; the 16 warps take interleaved rows of the block's quarter,
-// two at a time with every load issued before the FMAs (a warp's post values
-// of a row are broadcast reads of four at a time).  The warp partials are
-// added in double in a fixed order (the upper eight warps' first, through
-// shared memory) into the block's partial; dtrans_finish_kernel adds the
-// quarters in order plus c_{t+1} times the occupancy mass of k
-// (V_{t+1} = V'_{t+1} + c_{t+1}).
+// 32 x 32 tile of (k, k2), range of rows; n_split ranges, enough blocks to
+// cover the SMs).  Lane l of every warp owns column k2 = 32 tx + l and keeps
+// the 32 sums of its tile rows k = 32 ty + j in registers; the 16 warps take
+// interleaved rows of the block's range, two at a time with every load
+// issued before the FMAs (a warp's post values of a row are broadcast reads
+// of four at a time).  The warp partials are added in double in a fixed
+// order (the upper eight warps' first, through shared memory) into the
+// block's partial; dtrans_finish_kernel adds the ranges in order plus
+// c_{t+1} times the occupancy mass of k (V_{t+1} = V'_{t+1} + c_{t+1}).
 constexpr int kDtWarps = 16;
-constexpr int kDtSplit = 4;
 __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParams p) {
   __shared__ float s_acc[kDtWarps / 2][32][33];
   __shared__ float s_mass[kDtWarps][32];
@@ -304,13 +326,14 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
   const int tiles = (K + 31) / 32;
   const int ts = blockIdx.y, ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int part = blockIdx.z;
-  const int row0 = (int)((long long)MN * part / kDtSplit);
-  const int row1 = (int)((long long)MN * (part + 1) / kDtSplit);
+  const int row0 = (int)((long long)MN * part / p.n_split);
+  const int row1 = (int)((long long)MN * (part + 1) / p.n_split);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k2 = 32 * tx + lane, kb = 32 * ty;
   const int nk = min(32, K - kb);
   const float* post = p.post + (size_t)ts * MN * K;
-  const float* v = p.vnext + (size_t)ts * MN * K;
+  const float* v = p.vnext + (size_t)(ts / p.seg_len) * p.seg_stride +
+                   (size_t)(ts % p.seg_len) * MN * K;
   float acc[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
@@ -366,8 +389,8 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
   }
   __syncthreads();
   // this block's partial: [ts][part][k][k2] sums and [ts][part][k] masses
-  double* ps = p.part + ((size_t)ts * kDtSplit + part) * K * K;
-  double* pm = p.part_mass + ((size_t)ts * kDtSplit + part) * K;
+  double* ps = p.part + ((size_t)ts * p.n_split + part) * K * K;
+  double* pm = p.part_mass + ((size_t)ts * p.n_split + part) * K;
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int j = e >> 5, l = e & 31;
     const int k = kb + j, kk2 = 32 * tx + l;
@@ -385,7 +408,7 @@ __global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParam
   }
 }
 
-// dJ/dP_t[k][k2] = sum of the row quarters in order + c_{t+1} mass_t[k]
+// dJ/dP_t[k][k2] = sum of the row ranges in order + c_{t+1} mass_t[k]
 __global__ void dtrans_finish_kernel(const DTransParams p) {
   const int K = p.K;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -393,10 +416,9 @@ __global__ void dtrans_finish_kernel(const DTransParams p) {
   const int ts = (int)(i / ((long long)K * K));
   const int e = (int)(i - (long long)ts * K * K), k = e / K;
   double sv = 0.0, sm = 0.0;
-#pragma unroll
-  for (int q = 0; q < kDtSplit; ++q) {
-    sv += p.part[((size_t)ts * kDtSplit + q) * K * K + e];
-    sm += p.part_mass[((size_t)ts * kDtSplit + q) * K + k];
+  for (int q = 0; q < p.n_split; ++q) {
+    sv += p.part[((size_t)ts * p.n_split + q) * K * K + e];
+    sm += p.part_mass[((size_t)ts * p.n_split + q) * K + k];
   }
   p.d_trans[(size_t)ts * K * K + e] = (float)(sv + p.cnext[ts] * sm);
 }
@@ -464,7 +486,7 @@ cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream) {
   if (p.n_t == 0) return cudaSuccess;
   const int tiles = (p.K + 31) / 32;
-  dtrans_kernel<<<dim3(tiles * tiles, p.n_t, kDtSplit), 32 * kDtWarps, 0, stream>>>(p);
+  dtrans_kernel<<<dim3(tiles * tiles, p.n_t, p.n_split), 32 * kDtWarps, 0, stream>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long n = (long long)p.n_t * p.K * p.K;
