@@ -59,9 +59,11 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // post-decision occupancy are ordered before the flag by the CTA barrier and
 // one release store at GPU scope (cumulative over what the barrier ordered
 // before it; a separate fence ahead of the release cost 0.6 us per stage).
+// The last warp releases: the first warp, whose threads poll the sources,
+// is then not held up by the release's wait for the CTA's writes.
 __device__ __forceinline__ void publish_stage(int* flags, int epoch) {
   __syncthreads();
-  if (threadIdx.x == 0) st_release(flags + blockIdx.x, epoch);
+  if (threadIdx.x == blockDim.x - 32) st_release(flags + blockIdx.x, epoch);
 }
 
 // Wait until every CTA that can scatter into this CTA's rows [r0, r1) has
