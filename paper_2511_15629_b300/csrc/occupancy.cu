@@ -311,100 +311,120 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
 }
 
 // dJ/dP_t = post_t^T V_{t+1} over all rows (m, s): one block per (stage,
-// 32 x 32 tile of (k, k2), range of rows; n_split ranges, enough blocks to
-// cover the SMs).  Lane l of every warp owns column k2 = 32 tx + l and keeps
-// the 32 sums of its tile rows k = 32 ty + j in registers; the 16 warps take
-// interleaved rows of the block's range, two at a time with every load
-// issued before the FMAs (a warp's post values of a row are broadcast reads
-// of four at a time).  The warp partials are added in double in a fixed
-// order (the upper eight warps' first, through shared memory) into the
-// block's partial; dtrans_finish_kernel adds the ranges in order plus
-// c_{t+1} times the occupancy mass of k (V_{t+1} = V'_{t+1} + c_{t+1}).
-constexpr int kDtWarps = 16;
-__global__ void __launch_bounds__(32 * kDtWarps) dtrans_kernel(const DTransParams p) {
-  __shared__ float s_acc[kDtWarps / 2][32][33];
-  __shared__ float s_mass[kDtWarps][32];
+// 32 x 32 tile of (k, k2), range of rows; n_split ranges).  The block stages
+// its rows through shared memory 64 at a time (16-byte cp.async copies into
+// a double buffer when K is a multiple of 4, so the next rows land while
+// these are used); its 256 threads are four groups of 64, group g takes the
+// rows g, g + 4, ... of each chunk, and thread (i, j) of a group keeps the
+// 4 x 4 sums of k = kb + 4i.., k2 = k2b + 4j.. in registers (per row: two
+// 16-byte shared reads, 16 fmas; the threads with j = 0 also sum the
+// occupancy mass of their k).  The four groups' sums are added in double in
+// group order; dtrans_finish_kernel adds the ranges in order plus c_{t+1}
+// times the occupancy mass of k (V_{t+1} = V'_{t+1} + c_{t+1}).
+constexpr int kDtRows = 64;  // rows per shared chunk
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__global__ void __launch_bounds__(256) dtrans_kernel(const DTransParams p) {
+  // [2][64][32] post rows (columns kb..kb+31), then [2][64][32] V' rows
+  // (columns k2b..k2b+31); after the rows, the groups' sums [4][32][33]
+  __shared__ __align__(16) float sbuf[4 * kDtRows * 32];
+  __shared__ float sM[4][32];  // the groups' masses
+  auto sP = [&](int b, int r, int c) -> float* { return sbuf + (b * kDtRows + r) * 32 + c; };
+  auto sV = [&](int b, int r, int c) -> float* { return sbuf + ((2 + b) * kDtRows + r) * 32 + c; };
+  auto sR = [&](int g, int j, int l) -> float& { return sbuf[(g * 32 + j) * 33 + l]; };
   const int K = p.K, MN = p.MN;
   const int tiles = (K + 31) / 32;
   const int ts = blockIdx.y, ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int part = blockIdx.z;
   const int row0 = (int)((long long)MN * part / p.n_split);
   const int row1 = (int)((long long)MN * (part + 1) / p.n_split);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k2 = 32 * tx + lane, kb = 32 * ty;
-  const int nk = min(32, K - kb);
+  const int kb = 32 * ty, k2b = 32 * tx;
+  const int tid = threadIdx.x, grp = tid >> 6, lt = tid & 63;
+  const int mi = (lt >> 3) * 4, ni = (lt & 7) * 4;
   const float* post = p.post + (size_t)ts * MN * K;
   const float* v = p.vnext + (size_t)(ts / p.seg_len) * p.seg_stride +
                    (size_t)(ts % p.seg_len) * MN * K;
-  float acc[32];
+  const bool vec = (K & 3) == 0;
+  // chunk c of the range into buffer b: 64 rows x 32 columns of each array,
+  // zeros outside the range and beyond K
+  auto load_chunk = [&](int c, int b) {
+    const int rbase = row0 + c * kDtRows;
+    for (int q = tid; q < 2 * kDtRows * 8; q += 256) {
+      const int arr = q >= kDtRows * 8, qq = q - arr * kDtRows * 8;
+      const int r = qq >> 3, c4 = (qq & 7) * 4;
+      const int row = rbase + r, col = (arr ? k2b : kb) + c4;
+      float* dst = arr ? sV(b, r, c4) : sP(b, r, c4);
+      const float* src = (arr ? v : post) + (size_t)row * K + col;
+      if (vec && row < row1 && col + 4 <= K) {
+        cp_async16(dst, src);
+      } else {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-  float mass = 0.f;
-  const bool vec = (K & 3) == 0 && nk == 32;
-  for (int row = row0 + w; row < row1; row += 2 * kDtWarps) {
-    const int rb = row + kDtWarps;
-    const bool two = rb < row1;
-    const float* pa = post + (size_t)row * K + kb;
-    const float* pb = post + (size_t)(two ? rb : row) * K + kb;
-    const float va = k2 < K ? __ldg(v + (size_t)row * K + k2) : 0.f;
-    const float vb = (k2 < K && two) ? __ldg(v + (size_t)rb * K + k2) : 0.f;
-    if (lane < nk) mass += __ldg(pa + lane) + (two ? __ldg(pb + lane) : 0.f);
-    if (vec) {
-      const float4* a4 = reinterpret_cast<const float4*>(pa);
-      const float4* b4 = reinterpret_cast<const float4*>(pb);
-      float4 xa[8], xb[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        xa[q] = __ldg(a4 + q);
-        xb[q] = __ldg(b4 + q);
+        for (int e = 0; e < 4; ++e) dst[e] = (row < row1 && col + e < K) ? __ldg(src + e) : 0.f;
       }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        acc[4 * q] = fmaf(xb[q].x, vb, fmaf(xa[q].x, va, acc[4 * q]));
-        acc[4 * q + 1] = fmaf(xb[q].y, vb, fmaf(xa[q].y, va, acc[4 * q + 1]));
-        acc[4 * q + 2] = fmaf(xb[q].z, vb, fmaf(xa[q].z, va, acc[4 * q + 2]));
-        acc[4 * q + 3] = fmaf(xb[q].w, vb, fmaf(xa[q].w, va, acc[4 * q + 3]));
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < nk) acc[j] = fmaf(__ldg(pb + j), vb, fmaf(__ldg(pa + j), va, acc[j]));
     }
-  }
-  // fixed-order reduction: upper warps through shared memory into the lower,
-  // then the lower eight in double
-  const int half = kDtWarps / 2;
-  if (w >= half) {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float acc[4][4], mass[4];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) s_acc[w - half][j][lane] = acc[j];
-  }
-  s_mass[w][lane] = mass;
-  __syncthreads();
-  if (w < half) {
+  for (int i = 0; i < 4; ++i) {
+    mass[i] = 0.f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] += s_acc[w][j][lane];
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
   }
-  __syncthreads();
-  if (w < half) {
+  const int nchunk = (row1 - row0 + kDtRows - 1) / kDtRows;
+  if (nchunk > 0) load_chunk(0, 0);
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1;
+    if (c + 1 < nchunk) {
+      load_chunk(c + 1, b ^ 1);  // its buffer was last read before the barrier below
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = grp; r < kDtRows; r += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(sP(b, r, mi));
+      const float4 x = *reinterpret_cast<const float4*>(sV(b, r, ni));
+      const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int j = 0; j < 32; ++j) s_acc[w][j][lane] = acc[j];
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+      }
+      if (ni == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mass[i] += av[i];
+      }
+    }
+    __syncthreads();  // buffer b is refilled two chunks on (and sR overlays the rows)
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sR(grp, mi + i, ni + j) = acc[i][j];
+    if (ni == 0) sM[grp][mi + i] = mass[i];
   }
   __syncthreads();
   // this block's partial: [ts][part][k][k2] sums and [ts][part][k] masses
   double* ps = p.part + ((size_t)ts * p.n_split + part) * K * K;
   double* pm = p.part_mass + ((size_t)ts * p.n_split + part) * K;
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+  for (int e = tid; e < 32 * 32; e += 256) {
     const int j = e >> 5, l = e & 31;
-    const int k = kb + j, kk2 = 32 * tx + l;
+    const int k = kb + j, kk2 = k2b + l;
     if (k >= K || kk2 >= K) continue;
     double sv = 0.0;
 #pragma unroll
-    for (int q = 0; q < half; ++q) sv += (double)s_acc[q][j][l];
+    for (int q = 0; q < 4; ++q) sv += (double)sR(q, j, l);
     ps[(size_t)k * K + kk2] = sv;
     if (tx == 0 && l == 0) {
       double sm = 0.0;
 #pragma unroll
-      for (int q = 0; q < kDtWarps; ++q) sm += (double)s_mass[q][j];
+      for (int q = 0; q < 4; ++q) sm += (double)sM[q][j];
       pm[k] = sm;
     }
   }
@@ -488,7 +508,7 @@ cudaError_t launch_occupancy(const OccParams& p, int grid, int block, cudaStream
 cudaError_t launch_dtrans(const DTransParams& p, cudaStream_t stream) {
   if (p.n_t == 0) return cudaSuccess;
   const int tiles = (p.K + 31) / 32;
-  dtrans_kernel<<<dim3(tiles * tiles, p.n_t, p.n_split), 32 * kDtWarps, 0, stream>>>(p);
+  dtrans_kernel<<<dim3(tiles * tiles, p.n_t, p.n_split), 256, 0, stream>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long n = (long long)p.n_t * p.K * p.K;
