@@ -181,9 +181,13 @@ int esdp_objective(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, vo
 /* Objective J = sum_k mu0[k] V_1[0][s0][k] and its sensitivities by a
  * forward pass of the state-occupancy distribution under the stored argmax
  * policy (envelope theorem on eq. 5-6; exact away from ties).  With
- * ckpt_every = C > 0 the policies are recomputed segment by segment from the
- * V checkpoints; otherwise the whole horizon is recomputed once.  Uses the
- * inputs of the last esdp_solve.  In: mu0 [K].  Out (any may be NULL):
+ * ckpt_every = C > 0 the policies are recomputed from the V checkpoints, B
+ * segments of C stages at a time as the assets of one persistent launch (the
+ * segments are independent), holding B segments' policies, values and
+ * post-decision occupancies at once: B = the environment variable
+ * ESDP_GRAD_SEGMENTS, else as many as 1 GiB of that workspace holds (the
+ * result does not depend on B); otherwise the whole horizon is recomputed
+ * once.  Uses the inputs of the last esdp_solve.  In: mu0 [K].  Out (any may be NULL):
  *   J          [1]         double
  *   d_price    [T*K]       float   dJ/dprice[t][k]
  *   d_trans    [T*K*K]     float   dJ/dtrans[t][k][k2]
@@ -208,6 +212,8 @@ int esdp_grad(esdp_ctx* ctx, int32_t asset, const float* mu0, double* J, float* 
  * whose assets all have K = 63 or 64 use a kernel variant with the shared
  * EV row stride fixed at compile time (same results; ESDP_NO_KH=1 pins the
  * general variant).
+ * The launches of esdp_grad's segment re-sweeps (B copies of an asset with
+ * ckpt_every > 0) are timed the same way, once per shape of asset.
  * With the environment variable ESDP_SHAPE="R,block" (rows per thread
  * 4/6/8/9/10/12, threads per block) that shape is used without timing;
  * ESDP_EINVAL if it cannot be built for the context's assets.  The results
