@@ -335,6 +335,12 @@ int build_plan(esdp_ctx* c, const std::vector<int>& ids, int R, int block, int g
     flag_base += d.n_tiles;
   }
   plan->n_flags = flag_base;
+  if (plan->shape.kh == 0)
+    for (const AssetDev& d : plan->adev)
+      if ((d.K & 3) != 0 || d.parts == 1) {
+        plan->shape.kh = -1;
+        break;
+      }
   plan->sm_A = 0;
   plan->sm_A2 = (int)need_A;
   plan->sm_E = 2 * (int)need_A;

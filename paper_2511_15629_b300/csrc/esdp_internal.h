@@ -196,7 +196,10 @@ inline int pick_parts(int cells, int block, int chunks) {
 // Launch shape of one sweep.
 struct SweepShape {
   int R = 8;
-  int kh = 0;       // 32: every asset has K = 63 or 64 (the kernel variant with a fixed EV row stride)
+  int kh = 0;       // 32: every asset has K = 63 or 64 (the kernel variant with a fixed EV row
+                    // stride); -1: the variant with the paths only batches need (EV tiles of K
+                    // not a multiple of 4 copied eight loads at a time, one-part recovery of both
+                    // states per row), so that the other launches keep their code unchanged
   int block = 256;
   int grid = 0;
   size_t smem = 0;

@@ -776,6 +776,30 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
                      "l"(src + i)
                      : "memory");
     }
+  } else if (KH < 0) {
+    // (the batch variant) K not a multiple of 4: L2 loads of eight elements
+    // per thread in flight before their shared stores (a row of odd K gets a
+    // pad column)
+    for (int m = 0; m < M; ++m) {
+      const float* src = ev_t + ((size_t)m * N + lo) * K;
+      float* dst = sm.Es + ((size_t)m * rows + (lo - g0row)) * Ke;
+      const int n = (hi - lo) * K;
+      for (int i0 = tid; i0 < n; i0 += 8 * nth) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q * nth;
+          v[q] = i < n ? __ldcg(src + i) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q * nth;
+          if (i < n) dst[Ke == K ? i : i + i / K] = v[q];
+        }
+      }
+      if (Ke != K)
+        for (int r = tid; r < hi - lo; r += nth) dst[r * Ke + K] = NEG;  // pad column
+    }
   } else {
     for (int m = 0; m < M; ++m) {
       const float* src = ev_t + ((size_t)m * N + lo) * K;
@@ -993,6 +1017,40 @@ __device__ bool item_stage(PHASE_DECL const SweepParams& p, const AssetDev& as,
         }
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) store(2 * i + jo, h, bv[i], arg[i]);
+      } else if (KH < 0 && G == 1) {
+        // (the batch variant) one lane holds both states of every row: where the two states won
+        // in the same chunk, one scan reads each EV pair and payoff column
+        // once (the same two round-to-nearest operations per candidate)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int cx = bx[j], cy = by[j];
+          int ax, ay;
+          if (cx == cy && cx >= 0 && b * R + j < Wt) {
+            const bool second = cx >= n0;
+            const int u0 = (second ? cx - n0 : cx) * R;
+            const int a0 = second ? g1.a0 : g0.a0;
+            const int src = second ? g1.src : g0.src;
+            const int toff = second ? n0 * R : 0;
+            const float2* eb2 = reinterpret_cast<const float2*>(
+                sm.Es + ((size_t)src * rows + b * R + j + a0 + u0) * Ke + k0);
+            const float2* ep = ec + toff + u0;
+            int fx = R - 1, fy = R - 1;
+#pragma unroll
+            for (int i = R - 1; i >= 0; --i) {
+              const float2 ei = ep[i];
+              const float2 ev = eb2[(size_t)i * (Ke >> 1)];
+              if (fmaf(lam.x, ei.x, ei.y) + ev.x == best[j].x) fx = i;
+              if (fmaf(lam.y, ei.x, ei.y) + ev.y == best[j].y) fy = i;
+            }
+            ax = a0 + u0 + fx;
+            ay = a0 + u0 + fy;
+          } else {
+            ax = argmax_of(j, 0, best[j].x, cx);
+            ay = argmax_of(j, 1, best[j].y, cy);
+          }
+          store(j, 0, best[j].x, ax);
+          store(j, 1, best[j].y, ay);
+        }
       } else {
 #pragma unroll 2
         for (int e = part; e < 2 * R; e += G) {
@@ -1354,6 +1412,17 @@ cudaError_t launch_sweep(const SweepShape& s, const SweepParams& p, cudaStream_t
       default: return cudaErrorInvalidValue;
     }
   }
+  if (s.kh == -1) {
+    switch (s.R) {
+      case 4: return launch_R<4, -1>(s, p, stream);
+      case 6: return launch_R<6, -1>(s, p, stream);
+      case 8: return launch_R<8, -1>(s, p, stream);
+      case 9: return launch_R<9, -1>(s, p, stream);
+      case 10: return launch_R<10, -1>(s, p, stream);
+      case 12: return launch_R<12, -1>(s, p, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (s.kh != 0) return cudaErrorInvalidValue;
   switch (s.R) {
     case 4: return launch_R<4, 0>(s, p, stream);
@@ -1375,6 +1444,17 @@ int sweep_max_blocks_per_sm(int R, int kh, int block, size_t smem) {
       case 9: return max_blocks_R<9, 32>(block, smem);
       case 10: return max_blocks_R<10, 32>(block, smem);
       case 12: return max_blocks_R<12, 32>(block, smem);
+      default: return 0;
+    }
+  }
+  if (kh == -1) {
+    switch (R) {
+      case 4: return max_blocks_R<4, -1>(block, smem);
+      case 6: return max_blocks_R<6, -1>(block, smem);
+      case 8: return max_blocks_R<8, -1>(block, smem);
+      case 9: return max_blocks_R<9, -1>(block, smem);
+      case 10: return max_blocks_R<10, -1>(block, smem);
+      case 12: return max_blocks_R<12, -1>(block, smem);
       default: return 0;
     }
   }
