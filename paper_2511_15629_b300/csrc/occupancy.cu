@@ -121,6 +121,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr float kFxRho = 4294967296.f;  // 2^32 units per unit of occupancy mass
 constexpr double kFxRhoInv = 1.0 / 4294967296.0;
+constexpr float kFxRhoInvF = 1.0f / 4294967296.0f;
 constexpr int kPre = 4;  // entries per thread whose actions are loaded a stage ahead
 constexpr float kFxMaxRho = 1048576.f;  // 2^20: larger entries are reported
 
@@ -271,7 +272,10 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     // own rows of the post-decision occupancy, complete: fixed point to
     // float, for dJ/dP and (in shared memory when they fit) the contraction
     for (int i = e0; i < e1; i += nth) {
-      const float v = (float)((double)(long long)__ldcg(post_fx + i) * kFxRhoInv);
+      // one rounding of the integer to float32, then an exact scaling by
+      // 2^-32: the same value as through double, without this part's slow
+      // FP64 pipe
+      const float v = __ll2float_rn((long long)__ldcg(post_fx + i)) * kFxRhoInvF;
       post[i] = v;
       if (p.own_smem) spost[i - r0 * K] = v;
     }
