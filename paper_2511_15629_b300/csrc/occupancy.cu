@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   // slower than FP32), fixed-point shared sums, double from the warp sums on
   extern __shared__ double osm[];
   double* sacc = osm;                                       // [8] segment accumulators
-  double* wacc = osm + 8;                                   // [8 warps][3] stage warp sums
+  double* wacc = osm + 8;                                   // [8 warps][3] warp segment sums
   unsigned long long* skx = reinterpret_cast<unsigned long long*>(osm + 32);  // [K] dprice
   // [n_cc][A] cost partials of the segment: thread tid adds into copy
   // tid % n_cc, so that the many states that take the same action (full
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   }
   __syncthreads();
   int epoch = 0;
+  double wsum[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: the warp's segment sums
   // the stored actions of a thread's first kPre entries are loaded one stage
   // ahead, so that the scatter waits on no global load
   const int e0 = r0 * K + tid, e1 = r1 * K;
@@ -236,10 +237,10 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       dd += __shfl_xor_sync(0xffffffffu, dd, o);
       dsw += __shfl_xor_sync(0xffffffffu, dsw, o);
     }
-    if ((tid & 31) == 0) {
-      wacc[(tid >> 5) * 3 + 0] = (double)dc;
-      wacc[(tid >> 5) * 3 + 1] = (double)dd;
-      wacc[(tid >> 5) * 3 + 2] = (double)dsw;
+    if ((tid & 31) == 0) {  // the warp's segment sums (double, in stage order)
+      wsum[0] += (double)dc;
+      wsum[1] += (double)dd;
+      wsum[2] += (double)dsw;
     }
     // this CTA's partials of the stage (and, once, of the segment's costs):
     // plain stores, added up after the launch in a fixed order; a K sum is
@@ -258,16 +259,6 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     if (!wait_sources(p, r0, r1, epoch, &s_abort)) {
       asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
       return;
-    }
-    // the warp sums in warp order (written before the barrier of the wait)
-    if (tid == 0) {
-      for (int wq = 0; wq < (nth >> 5); ++wq) {
-        sacc[0] += wacc[wq * 3 + 0];
-        sacc[1] += wacc[wq * 3 + 1];
-        sacc[4] += wacc[wq * 3 + 2];
-      }
-      if (t == p.t_hi)
-        for (int q = 0; q < 8; ++q) p.part_acc[(size_t)blockIdx.x * 8 + q] = sacc[q];
     }
     // own rows of the post-decision occupancy, complete: fixed point to
     // float, for dJ/dP and (in shared memory when they fit) the contraction
@@ -311,6 +302,22 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       if (p.own_smem && t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's part of P_{t+1}
+  }
+  // the segment accumulators: the warps' sums added in warp order (the FP64
+  // additions once per segment, off the stages' critical path)
+  if ((tid & 31) == 0) {
+    wacc[(tid >> 5) * 3 + 0] = wsum[0];
+    wacc[(tid >> 5) * 3 + 1] = wsum[1];
+    wacc[(tid >> 5) * 3 + 2] = wsum[2];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int wq = 0; wq < (nth >> 5); ++wq) {
+      sacc[0] += wacc[wq * 3 + 0];
+      sacc[1] += wacc[wq * 3 + 1];
+      sacc[4] += wacc[wq * 3 + 2];
+    }
+    for (int q = 0; q < 8; ++q) p.part_acc[(size_t)blockIdx.x * 8 + q] = sacc[q];
   }
 }
 
