@@ -1337,7 +1337,7 @@ extern "C" int esdp_grad(esdp_ctx* c, int32_t asset, const float* mu0, double* J
     op.d_price = (double*)dprice64;
     op.acc = (double*)acc;
     op.d_cost = (double*)dcost64;
-    op.part = (double*)opart;
+    op.part = (long long*)opart;
     op.part_cost = (double*)opart_cost;
     op.part_acc = (double*)opart_acc;
     op.flags = (int*)bar;

@@ -275,7 +275,7 @@ struct OccParams {
   double* d_price;        // [T][K] (accumulated)
   double* acc;            // [5]: d_eta_c, d_eta_d, (two unused slots), d_switch
   double* d_cost;         // [A] (accumulated)
-  double* part;           // [C][grid][K] per-CTA stage partials of dprice
+  long long* part;        // [C][grid][K] per-CTA stage partials of dprice (fixed point, fx_e units)
   double* part_cost;      // [grid][A] per-CTA segment partials of d_cost
   double* part_acc;       // [grid][8] per-CTA segment partials of acc
   int* flags;             // [grid] last stage whose scatter each CTA published (zero on entry)

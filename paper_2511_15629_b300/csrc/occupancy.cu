@@ -155,7 +155,6 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   // own occupancy rows: in shared memory for the whole segment when they
   // fit (the scatter reads and the contraction writes only these rows)
   float* rho = p.own_smem ? srho - r0 * K : p.rho;
-  const double inv_fx_e = 1.0 / (double)p.fx_e;  // a power of two: exact
   if (tid == 0) s_abort = 0;
   for (int a = tid; a < n_cc * p.A; a += nth) scx[a] = 0ull;
   if (tid < 8) sacc[tid] = 0.0;  // summed over the segment
@@ -168,7 +167,8 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
   }
   __syncthreads();
   int epoch = 0;
-  double wsum[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: the warp's segment sums
+  // lane 0 of each warp: the warp's segment sums and their compensations
+  float wsum[3] = {0.f, 0.f, 0.f}, wcmp[3] = {0.f, 0.f, 0.f};
   // the stored actions of a thread's first kPre entries are loaded one stage
   // ahead, so that the scatter waits on no global load
   const int e0 = r0 * K + tid, e1 = r1 * K;
@@ -237,17 +237,22 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       dd += __shfl_xor_sync(0xffffffffu, dd, o);
       dsw += __shfl_xor_sync(0xffffffffu, dsw, o);
     }
-    if ((tid & 31) == 0) {  // the warp's segment sums (double, in stage order)
-      wsum[0] += (double)dc;
-      wsum[1] += (double)dd;
-      wsum[2] += (double)dsw;
+    if ((tid & 31) == 0) {  // the warp's segment sums: compensated float32, in stage order
+      const float x[3] = {dc, dd, dsw};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float y = x[q] - wcmp[q];
+        const float u = wsum[q] + y;
+        wcmp[q] = (u - wsum[q]) - y;
+        wsum[q] = u;
+      }
     }
     // this CTA's partials of the stage (and, once, of the segment's costs):
     // plain stores, added up after the launch in a fixed order; a K sum is
     // cleared by the thread that read it, before the next stage's scatter
-    double* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
+    long long* pr = p.part + ((size_t)ts * gridDim.x + blockIdx.x) * K;
     for (int i = tid; i < K; i += nth) {
-      pr[i] = (double)(long long)skx[i] * inv_fx_e;
+      pr[i] = (long long)skx[i];  // fixed point: turned into double by the reduction
       skx[i] = 0ull;
     }
     if (t == p.t_hi)
@@ -303,13 +308,10 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's part of P_{t+1}
   }
-  // the segment accumulators: the warps' sums added in warp order (the FP64
-  // additions once per segment, off the stages' critical path)
-  if ((tid & 31) == 0) {
-    wacc[(tid >> 5) * 3 + 0] = wsum[0];
-    wacc[(tid >> 5) * 3 + 1] = wsum[1];
-    wacc[(tid >> 5) * 3 + 2] = wsum[2];
-  }
+  // the segment accumulators: the warps' sums added in warp order in double
+  // (this part's FP64 pipe is slow: once per segment, off the stages' path)
+  if ((tid & 31) == 0)
+    for (int q = 0; q < 3; ++q) wacc[(tid >> 5) * 3 + q] = (double)wsum[q] - (double)wcmp[q];
   __syncthreads();
   if (tid == 0) {
     for (int wq = 0; wq < (nth >> 5); ++wq) {
@@ -469,7 +471,9 @@ __global__ void occ_reduce_kernel(const OccParams p, int grid) {
   double s = 0.0;
   if (o < n_price) {
     const int ts = o / K, k = o - ts * K;
-    for (int b = lane; b < grid; b += 32) s += p.part[((size_t)ts * grid + b) * K + k];
+    const double inv_fx_e = 1.0 / (double)p.fx_e;  // a power of two: exact
+    for (int b = lane; b < grid; b += 32)
+      s += (double)p.part[((size_t)ts * grid + b) * K + k] * inv_fx_e;
   } else if (o < n_price + 5) {
     const int q = o - n_price;
     for (int b = lane; b < grid; b += 32) s += p.part_acc[(size_t)b * 8 + q];
