@@ -389,6 +389,47 @@ def test_gradient_segment_groups_agree(monkeypatch):
             np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
 
 
+def test_gradient_segment_groups_on_tensor_path(monkeypatch):
+    """The grouped segment re-sweeps with the EV contraction pinned to
+    tcgen05 (K = 16): the gradient matches the FP64 occupancy pass under the
+    GPU's decisions, and re-sweeping the four segments one at a time gives
+    the same bits as all four in one launch."""
+    monkeypatch.setenv("ESDP_EV", "tc")
+    inst = I.random_instance(58, 22, 180, 16, 10, 12, 1, neg_prob=0.2)
+    inst.s0 = 90
+    inst.ckpt_every = 6
+    inst.policy_bytes = 2
+    _grad_check(inst, tie_free=False)
+    s, _ = solve_gpu(inst)
+    assert s.launch_info()["ev"] == "tcgen05"
+    mu0 = np.full(inst.K, 1.0 / inst.K, np.float32)
+    ref = s.grad(0, mu0, extra=True)
+    monkeypatch.setenv("ESDP_GRAD_SEGMENTS", "1")
+    one = s.grad(0, mu0, extra=True)
+    for x, y in zip(ref, one):
+        np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_batch_variant_odd_states_values_and_policies():
+    """Assets with K not a multiple of 4 (odd K, one and two modes) run the
+    batch variant of the sweep kernel: its EV-tile copy, its one-part argmax
+    recovery and its flat output stores.  Values and stored decisions of
+    every stage match the FP64 oracle."""
+    assets = [I.random_instance(90 + j, 9, n, k, d1, d2, m, neg_prob=0.2)
+              for j, (n, k, d1, d2, m) in enumerate([(230, 5, 14, 11, 1), (161, 7, 9, 9, 2),
+                                                     (97, 9, 20, 6, 1), (301, 3, 4, 30, 2),
+                                                     (64, 11, 8, 8, 1)])]
+    s = E.Solver(assets)
+    V1s = s.solve_instances()
+    for j, (inst, V1) in enumerate(zip(assets, V1s)):
+        r = O.solve(inst, keep_EV=True, nthreads=NTHREADS)
+        scale = _scale(r["V1"])
+        assert_values(V1, r["V1"], scale, inst.name)
+        pol = np.stack([s.policy(j, t) for t in range(1, inst.T + 1)])
+        assert_policy(pol, r["policy"], r["gap"], scale, what=f"{inst.name} policy",
+                      inst=inst, EV=r["EV"])
+
+
 def test_gradient_rejects_occupancy_beyond_fixed_point_range():
     """An initial distribution with entries above 2^20 cannot be added in the
     scatter's fixed point: the call reports ESDP_ENUMERIC instead of
