@@ -24,6 +24,13 @@
 // Float32 values are kept centred: V'_t = V_t - c_t with a scalar level
 // c_t = c_{t+1} + EV'_t[ref] carried in double (the same on every tile), and
 // the payoff of price state k absorbs c_{t+1} rowsum(P_t)[k] - c_t.
+//
+// The kernel is compiled as sweep_kernel<R, KH>: R rows per thread, and KH =
+// 32 (every asset has K = 63 or 64: the shared EV row stride is a compile-time
+// constant), -1 (the batch variant: paths that only launches with K not a
+// multiple of 4 or one action part take) or 0 (general).  The variants give
+// the same results; keeping rarely taken paths out of a variant keeps its
+// loop's register allocation as it is.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
