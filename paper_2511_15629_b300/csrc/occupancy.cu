@@ -265,46 +265,63 @@ __global__ void __launch_bounds__(256) occ_kernel(const OccParams p) {
       asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
       return;
     }
-    // own rows of the post-decision occupancy, complete: fixed point to
-    // float, for dJ/dP and (in shared memory when they fit) the contraction
-    for (int i = e0; i < e1; i += nth) {
-      // one rounding of the integer to float32, then an exact scaling by
-      // 2^-32: the same value as through double, without this part's slow
-      // FP64 pipe
-      const float v = __ll2float_rn((long long)__ldcg(post_fx + i)) * kFxRhoInvF;
-      post[i] = v;
-      if (p.own_smem) spost[i - r0 * K] = v;
-    }
-    __syncthreads();
-    // contraction of the post-decision occupancy with P_t (own rows); entry
-    // i of rho is written here and read by the next scatter in the same
-    // thread, and every other shared buffer of the next stage is reused only
-    // behind its release barrier, so no barrier closes the stage
-    for (int i = e0; i < e1; i += nth) {
-      const int row = i / K, k2 = i - row * K;
-      float acc = 0.f;
-      if (p.own_smem) {
-        // in ascending k, one fma per term; the loads of eight terms are
-        // issued ahead of their fmas
-        const float* prw = spost + (size_t)(row - r0) * K;
-        int k = 0;
-        for (; k + 8 <= K; k += 8) {
-          float a8[8], b8[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            a8[j] = prw[k + j];
-            b8[j] = Ps[(k + j) * K + k2];
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc = fmaf(a8[j], b8[j], acc);
-        }
-        for (; k < K; ++k) acc = fmaf(prw[k], Ps[k * K + k2], acc);
-      } else {
-        const float* prw = post + (size_t)row * K;
-        for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(prw + k), Ps[k * K + k2], acc);
+    if (p.own_smem && K == 32 && (nth & 31) == 0) {
+      // K = 32: a warp's entries of one pass are the 32 states of one row,
+      // so each lane keeps its converted entry in a register and the row's
+      // terms reach the other lanes by shuffles (no shared copy, no barrier);
+      // each output is still summed in ascending k with one fma per term
+      for (int i = e0; i < e1; i += nth) {
+        const float v = __ll2float_rn((long long)__ldcg(post_fx + i)) * kFxRhoInvF;
+        post[i] = v;
+        const int k2 = i & 31;
+        float acc = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) acc = fmaf(__shfl_sync(0xffffffffu, v, k), Ps[k * 32 + k2], acc);
+        rho[i] = acc;
+        if (t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
       }
-      rho[i] = acc;
-      if (p.own_smem && t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
+    } else {
+      // own rows of the post-decision occupancy, complete: fixed point to
+      // float, for dJ/dP and (in shared memory when they fit) the contraction
+      for (int i = e0; i < e1; i += nth) {
+        // one rounding of the integer to float32, then an exact scaling by
+        // 2^-32: the same value as through double, without this part's slow
+        // FP64 pipe
+        const float v = __ll2float_rn((long long)__ldcg(post_fx + i)) * kFxRhoInvF;
+        post[i] = v;
+        if (p.own_smem) spost[i - r0 * K] = v;
+      }
+      __syncthreads();
+      // contraction of the post-decision occupancy with P_t (own rows); entry
+      // i of rho is written here and read by the next scatter in the same
+      // thread, and every other shared buffer of the next stage is reused only
+      // behind its release barrier, so no barrier closes the stage
+      for (int i = e0; i < e1; i += nth) {
+        const int row = i / K, k2 = i - row * K;
+        float acc = 0.f;
+        if (p.own_smem) {
+          // in ascending k, one fma per term; the loads of eight terms are
+          // issued ahead of their fmas
+          const float* prw = spost + (size_t)(row - r0) * K;
+          int k = 0;
+          for (; k + 8 <= K; k += 8) {
+            float a8[8], b8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              a8[j] = prw[k + j];
+              b8[j] = Ps[(k + j) * K + k2];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc = fmaf(a8[j], b8[j], acc);
+          }
+          for (; k < K; ++k) acc = fmaf(prw[k], Ps[k * K + k2], acc);
+        } else {
+          const float* prw = post + (size_t)row * K;
+          for (int k = 0; k < K; ++k) acc = fmaf(__ldcg(prw + k), Ps[k * K + k2], acc);
+        }
+        rho[i] = acc;
+        if (p.own_smem && t == p.t_hi) p.rho[i] = acc;  // the next segment starts from it
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's part of P_{t+1}
   }
