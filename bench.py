@@ -62,7 +62,7 @@ def parse():
                     help="per-stage cycles of each sweep phase (config3 and config2) from the "
                          "library built with per-phase clock counters; prints one JSON line")
     ap.add_argument("--profile-case", default="",
-                    help="config3 | config3-64 | config3-64-A101 | config2 | config5-grad | table3-20h: "
+                    help="config3 | config3-64 | config3-64-A101 | config2 | config4-64x24 | config5-grad | table3-20h: "
                          "one solve inside "
                          "the NVTX range 'esdp_profile' "
                          "(for ncu --nvtx --nvtx-include esdp_profile/)")
@@ -774,6 +774,28 @@ def run_profile_case(name):
                           s0=full.s0)
     elif name == "config2":
         inst = I.config2()
+    elif name == "config4-64x24":
+        # 64 of the portfolio's assets (full N, K, A) on a 24-stage horizon,
+        # one launch: the batch kernel variant at a size ncu can replay
+        assets = []
+        for a in I.config4(64):
+            a.T = 24
+            a.price = np.ascontiguousarray(a.price[:24])
+            a.trans = np.ascontiguousarray(a.trans[:24])
+            assets.append(a)
+        d = {k: torch.from_numpy(v).to("cuda") for k, v in E.concat_inputs(assets).items()}
+        V1 = torch.empty(sum(a.n_modes * a.N * a.K for a in assets), device="cuda")
+        s = E.Solver(assets, device_ptrs=True)
+        s.autotune()
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("esdp_profile")
+        s.solve(d["price"], d["trans"], d["cost"], d["terminal"], V1)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        print(json.dumps({"profile_case": name, "launch": s.launch_info()}))
+        return
     elif name == "config5-grad":
         # forward solve and the occupancy adjoint of the gradient asset
         inst = I.config5()
