@@ -1064,6 +1064,42 @@ def test_price_gradient_vs_gpu_central_differences():
         assert fd == pytest.approx(dp[t, k], rel=2e-2, abs=noise), (t, k, fd, dp[t, k])
 
 
+def test_transition_gradient_vs_gpu_central_differences():
+    """dJ/dP from the occupancy adjoint against central differences of the
+    GPU's own forward solve: one transition entry P_t[k][k2] moved by +-h
+    (h = 1e-4, the float32 step actually taken) on a tie-free instance (every
+    top-two gap far above what the step can move, h max|V|), for the four
+    entries with the largest sensitivity; the quotient's float32 noise
+    allowed for as in the price check."""
+    make = lambda: I.random_instance(63, 4, 60, 3, 4, 4, 1, neg_prob=0.0, cost="linear",
+                                     s_max=59.0)
+    inst = make()
+    inst.s0 = 30
+    h = 1e-4
+    r = O.solve(inst, keep_V=True, nthreads=NTHREADS)
+    v_max = float(np.abs(r["V"]).max())
+    assert r["gap"][np.isfinite(r["gap"])].min() > 20 * h * v_max, "the seed must be tie-free"
+    s, _ = solve_gpu(inst)
+    J0, _, dt = s.grad(0, inst.mu0)[:3]
+    dt = np.asarray(dt, np.float64).reshape(inst.T, inst.K, inst.K)
+    order = np.argsort(-np.abs(dt).ravel())[:4]
+    for flat in order:
+        t, k, k2 = np.unravel_index(flat, dt.shape)
+        vals = []
+        for sign in (1.0, -1.0):
+            pert = make()
+            pert.s0 = 30
+            p64 = pert.trans.astype(np.float64)
+            p64[t, k, k2] += sign * h
+            pert.trans = p64.astype(np.float32)
+            step = float(pert.trans[t, k, k2]) - float(inst.trans[t, k, k2])
+            _, V1 = solve_gpu(pert)
+            vals.append((float(np.dot(inst.mu0.astype(np.float64), V1[0, inst.s0, :])), step))
+        fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        noise = 1e-7 * abs(float(J0[0])) / h
+        assert fd == pytest.approx(dt[t, k, k2], rel=2e-2, abs=noise), (t, k, k2, fd, dt[t, k, k2])
+
+
 def test_autograd_checkpointed_int16():
     import torch
     from paper_2511_15629_b300.autograd import StorageObjective
