@@ -82,6 +82,37 @@ def test_noalloc_mma_path(monkeypatch, K):
     s.close()
 
 
+@pytest.mark.parametrize("K,modes", [(64, 1), (63, 2)])
+def test_noalloc_fixed_stride_variant(monkeypatch, K, modes):
+    """Assets with K = 63 or 64 run the sweep variant with a compile-time EV
+    row stride inside the allocation-free entry point too; with the FP32
+    SIMT contraction pinned in both entry points (the same arithmetic), it
+    gives the regular solve's values and policies, on two calls in a row."""
+    import torch
+    monkeypatch.setenv("ESDP_EV", "simt")
+    inst = I.random_instance(95 + K, 5, 410, K, 21, 17, modes, neg_prob=0.25,
+                             cost="nonconvex")
+    d = _inputs(inst)
+    MNK = inst.n_modes * inst.N * inst.K
+    ref = torch.empty(MNK, device="cuda")
+    s = E.Solver([inst], device_ptrs=True)
+    assert s.launch_info()["ev"] == "simt"
+    s.solve(d["price"], d["trans"], d["cost"], d["terminal"], ref)
+    ref_pol = torch.empty(inst.T * MNK, dtype=torch.int32, device="cuda")
+    for t in range(1, inst.T + 1):
+        s.policy(0, t, ref_pol[(t - 1) * MNK:t * MNK])
+    torch.cuda.synchronize()
+    s.close()
+    scale = float(ref.abs().max())
+    for call in range(2):
+        V1 = torch.full((MNK,), float("nan"), device="cuda")
+        pol = torch.full((inst.T * MNK,), -7, dtype=torch.int32, device="cuda")
+        E.solve_noalloc(inst, d["price"], d["trans"], d["cost"], d["terminal"], V1, pol)
+        err = float((V1 - ref).abs().max()) / scale
+        assert err <= VTOL, f"call {call}: rel error {err:.3e}"
+        assert torch.equal(pol, ref_pol), f"call {call}: policies differ"
+
+
 def test_noalloc_allocates_no_device_memory():
     """After a first call (which loads the library's device code, and with
     it the fixed workspace, on this device), further calls change neither
