@@ -732,6 +732,34 @@ def test_every_rows_per_thread_variant(monkeypatch, R, block, K):
     assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale, inst=inst, EV=r["EV"])
 
 
+VARIANT_CASES = [
+    # R, block, K, modes: K = 63 or 64 take the fixed-stride variant, K = 13
+    # (not a multiple of 4) the batch variant
+    (4, 256, 64, 1), (8, 512, 64, 2), (9, 256, 63, 1), (10, 384, 64, 1), (12, 256, 63, 1),
+    (4, 256, 13, 2), (6, 384, 13, 1), (8, 256, 13, 1), (9, 384, 13, 2), (10, 256, 13, 1),
+    (12, 512, 13, 1),
+]
+
+
+@pytest.mark.parametrize("R,block,K,M", VARIANT_CASES,
+                         ids=[f"R{c[0]}b{c[1]}K{c[2]}M{c[3]}" for c in VARIANT_CASES])
+def test_rows_per_thread_in_every_kernel_variant(monkeypatch, R, block, K, M):
+    """The rows-per-thread variants of the fixed-stride sweep (K = 63, 64)
+    and of the batch sweep (K not a multiple of 4), pinned through
+    ESDP_SHAPE, match the oracle's values and policies."""
+    inst = I.random_instance(700 + R + K, 5, 301, K, 28, 26, M, neg_prob=0.2, cost="nonconvex")
+    monkeypatch.setenv("ESDP_SHAPE", f"{R},{block}")
+    s = E.Solver([inst])
+    s.autotune()
+    info = s.launch_info()
+    assert info["rows_per_thread"] == R and info["block"] == block
+    V1 = s.solve_instances()[0]
+    r = O.solve(inst, keep_EV=True, nthreads=NTHREADS)
+    scale = _scale(r["V1"])
+    assert_values(V1, r["V1"], scale)
+    assert_policy(gpu_policies(s, inst), r["policy"], r["gap"], scale, inst=inst, EV=r["EV"])
+
+
 # ------------------------------------------------- EV contraction paths
 
 EV_CASES = [
