@@ -372,6 +372,10 @@ def run_esdp(args, rank, world):
             "rates (alu_probe)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = sweep_evals_s / alu_peak_evals(n_sm, clocks["sm_mhz"])
+    # the planning figure of two FP32-pipe instructions per evaluation (an add,
+    # then a max, without packed or three-input forms): half the issue ceiling,
+    # reported beside the headline fraction for comparison only
+    roof["frac_two_instr_per_eval"] = sweep_evals_s / (peak / 2)
     info = s.launch_info()
     s.close()
     del d, V1
